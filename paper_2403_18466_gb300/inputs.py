@@ -57,6 +57,12 @@ def random_velocity_field(ny: int, nx: int, seed: int, k0: float = 8.0, urms: fl
         amp_psi = np.where(kk > 0, amp_u / np.maximum(kk, 1e-30), 0.0)
     theta = rng.uniform(0.0, 2.0 * np.pi, size=kk.shape)
     psi_hat = amp_psi * np.exp(1j * theta)
+    # Nyquist rows/columns have no Hermitian partner: drop them so that the
+    # real part stays divergence-free
+    if ny % 2 == 0:
+        psi_hat[ny // 2, :] = 0.0
+    if nx % 2 == 0:
+        psi_hat[:, nx // 2] = 0.0
     # scale wavenumbers to radians per lattice unit for the derivative
     sy, sx = 2.0 * np.pi / ny, 2.0 * np.pi / nx
     ux = np.real(np.fft.ifft2(1j * (KY * sy) * psi_hat))
