@@ -1,0 +1,179 @@
+/*
+ * lbm.h -- C ABI of liblbm: a D2Q9 lattice-Boltzmann step with BGK,
+ * Smagorinsky-BGK and learned (MLP) collisions, its adjoint, and the data
+ * pipeline kernels, hand-written for sm_103a.
+ *
+ * Paper: "Kinetic data-driven approach to turbulence subgrid modeling"
+ * (arXiv 2403.18466).  The operations follow its statement of the method:
+ *   - lattice Boltzmann equation, stream/collide split: Methods, Eq. S2;
+ *   - BGK collision: Eq. S3; equilibrium: Eq. S4; EDM forcing: Eq. S5;
+ *   - Smagorinsky relaxation time: SI section 1 (Eq. S7 and the strain
+ *     from the non-equilibrium stress; closed form derived in the design doc);
+ *   - learned collision with mass/momentum projection: Eqs. S10-S12;
+ *   - unrolled training and its loss: SI section 2, Eq. S13;
+ *   - coarse-graining filter and rescaled tau: SI section 2, Eq. S9.
+ *
+ * Conventions common to every entry point
+ *   - D2Q9 velocities, in this order (index: c_x, c_y):
+ *       0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+ *     weights 4/9 (i=0), 1/9 (i=1..4), 1/36 (i=5..8); c_s^2 = 1/3; dt = dx = 1.
+ *   - Population arrays are FP32 structure-of-arrays, index [b][i][y][x]
+ *     (x fastest), plane stride nx*ny, batch stride 9*nx*ny.  Scalar fields
+ *     (rho, u_x, u_y, targets) are [b][y][x].
+ *   - All array pointers are DEVICE pointers unless the name says host.
+ *     The caller owns every array it passes; the library never frees them.
+ *   - Every call is asynchronous on the context's stream unless documented
+ *     otherwise, and returns LBM_OK (0) or a negative LBM_ERR_* code.
+ *     Nothing throws across the ABI.  Argument errors are detected on the
+ *     host before any launch.
+ *   - Periodic boundaries in x and y.
+ *   - Kolmogorov body force F = (F0 sin(2 pi m y / ny), 0), applied by EDM
+ *     after the collision at every step of every kind (F0 = 0 disables it).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)         /* invalid argument (null pointer, size, kind) */
+#define LBM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define LBM_ERR_UNSUPPORTED (-3) /* valid but not supported by this build */
+#define LBM_ERR_UNSTABLE (-4)    /* a node reached |u| >= 0.4 or a non-finite value */
+#define LBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+  LBM_BGK = 0,      /* Eq. S3 */
+  LBM_SMAG = 1,     /* Smagorinsky-BGK, SI section 1 */
+  LBM_MLP_BF16 = 2, /* Eq. S10, MLP on the tensor cores (BF16 in, FP32 accumulate) */
+  LBM_MLP_F32 = 3   /* Eq. S10, MLP in FP32 on the CUDA cores */
+} lbm_collision;
+
+typedef struct {
+  int nx, ny, batch;   /* grid and number of independent lattices (>= 1 each) */
+  double tau;          /* relaxation time, > 0.5 (Eq. S3, S6) */
+  double smag_cs;      /* Smagorinsky constant C_s (used by LBM_SMAG) */
+  double smag_delta;   /* filter width Delta in lattice units (LBM_SMAG) */
+  double force_amp;    /* Kolmogorov amplitude F0 */
+  int force_mode;      /* Kolmogorov wavenumber m */
+  int flags;           /* reserved, must be 0 */
+} lbm_params;
+
+/* MLP 9 -> 64 -> 64 -> 9, tanh hidden layers, linear output (Eq. S10 network
+ * with this library's widths).  Device pointers, row-major [out][in]:
+ * w1[64][9], b1[64], w2[64][64], b2[64], w3[9][64], b3[9].
+ * dtype 0 = FP32 (both MLP kinds), 1 = BF16 (LBM_MLP_BF16 only).  The
+ * weights are read at launch, never copied or retained. */
+typedef struct {
+  const void *w1, *b1, *w2, *b2, *w3, *b3;
+  int dtype;
+} lbm_weights;
+
+#define LBM_MLP_HIDDEN 64
+#define LBM_MLP_NPARAMS 5385 /* packed order w1, b1, w2, b2, w3, b3 */
+
+/* Create a context over two caller-owned device state buffers of
+ * 9*nx*ny*batch floats each (ping-pong), on `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream).  The buffers hold the library's internal
+ * state representation: post-collision populations minus the weights w_i
+ * (the pull scheme stores f_post at time t; the pre-collision populations
+ * at t+1 are the streamed values).  Use lbm_set_state / lbm_get_state to
+ * move populations in and out.  Allocates the context and a small device
+ * scratch area (status flag, force table, reduction partials), freed by
+ * lbm_destroy.  Synchronous. */
+int lbm_init(lbm_ctx **out, const lbm_params *p, float *f_buf0, float *f_buf1,
+             void *cuda_stream);
+
+/* Release the context and its scratch (not the caller's buffers). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Load pre-collision populations f_pre [b][i][y][x] (unshifted) as the
+ * current state.  Anti-streams them (SI section 2, step 4) into the current
+ * buffer. */
+int lbm_set_state(lbm_ctx *ctx, const float *f_pre);
+
+/* Write the current pre-collision populations (streamed, unshifted) to
+ * f_pre [b][i][y][x]. */
+int lbm_get_state(lbm_ctx *ctx, float *f_pre);
+
+/* Set the state to the equilibrium feq(rho, u) (Eq. S4) of the given fields
+ * [b][y][x] as pre-collision populations. */
+int lbm_init_equilibrium(lbm_ctx *ctx, const float *rho, const float *ux, const float *uy);
+
+/* Advance n >= 0 steps: per node, pull-stream (Eq. S2), collide with `kind`
+ * (Eq. S3 / SI sec. 1 / Eq. S10-S12), add the EDM force (Eq. S5), store.
+ * `w` is required for the MLP kinds and ignored otherwise.  A node whose
+ * velocity reaches |u| >= 0.4, or becomes non-finite, sets the sticky
+ * status flag read by lbm_status. */
+int lbm_step(lbm_ctx *ctx, int n, lbm_collision kind, const lbm_weights *w);
+
+/* Density and velocity u = j / rho of the current pre-collision populations
+ * into rho, ux, uy [b][y][x] (any of them may be NULL). */
+int lbm_moments(lbm_ctx *ctx, float *rho, float *ux, float *uy);
+
+/* Device pointer of the buffer holding the current state (internal
+ * representation, see lbm_init), or NULL. */
+float *lbm_state_buffer(lbm_ctx *ctx);
+
+/* Synchronise the stream and return LBM_ERR_UNSTABLE if any step since the
+ * last lbm_clear_status flagged a node, a pending CUDA error as
+ * LBM_ERR_CUDA, else LBM_OK.  Synchronous. */
+int lbm_status(lbm_ctx *ctx);
+int lbm_clear_status(lbm_ctx *ctx);
+
+/* Velocity loss of the current state against targets (utx, uty) [b][y][x]:
+ * L = 1/(2 N B) sum |u - u_t|^2 with u = j/rho of the pre-collision
+ * populations (velocity form of Eq. S13), written to loss[0] (device,
+ * deterministic two-pass reduction), and, if dL_df is not NULL, its
+ * gradient with respect to the pre-collision populations [b][i][y][x]. */
+int lbm_velocity_loss(lbm_ctx *ctx, const float *utx, const float *uty, float *loss,
+                      float *dL_df);
+
+/* Bytes of the workspace lbm_forward_record / lbm_backward need for an
+ * n-step unroll with a checkpoint every ckpt_every steps. */
+size_t lbm_record_bytes(const lbm_params *p, int n, int ckpt_every);
+
+/* Unrolled training forward (SI section 2): advance n steps with the FP32
+ * learned collision, storing the state every ckpt_every steps into `ws`
+ * (device, >= lbm_record_bytes).  The context ends at step n, as after
+ * lbm_step(n, LBM_MLP_F32). */
+int lbm_forward_record(lbm_ctx *ctx, int n, int ckpt_every, const lbm_weights *w, void *ws,
+                       size_t ws_bytes);
+
+/* Hand-written adjoint of the recorded unroll.  dL_df_final is dL/d(pre-
+ * collision populations) at the final time (e.g. from lbm_velocity_loss).
+ * Recomputes each segment from its checkpoint, runs the per-step adjoint
+ * (transpose of the pull = push; vector-Jacobian product of the learned
+ * collision), and writes dL/dtheta (LBM_MLP_NPARAMS floats, packed w1, b1,
+ * w2, b2, w3, b3; overwritten; deterministic) to dW and, if not NULL,
+ * dL/d(pre-collision populations at the start) to dL_df0.  Uses the `ws`
+ * of the matching lbm_forward_record (n and ckpt_every are remembered by the
+ * context); the context's state is not changed. */
+int lbm_backward(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights *w, void *ws,
+                 size_t ws_bytes, float *dW, float *dL_df0);
+
+/* Coarse-graining filter (SI section 2, with a box average as filter phi):
+ * f_coarse[b][i][J][I] = mean over the cg x cg block of the CURRENT
+ * pre-collision populations of ctx_fine.  nx, ny must be multiples of cg. */
+int lbm_box_filter(lbm_ctx *ctx_fine, int cg, float *f_coarse);
+
+/* Host-buffer convenience: copy f_pre_host (pinned or pageable host memory,
+ * [b][i][y][x]) in, advance n steps with `kind`, copy the final rho, ux, uy
+ * to host arrays (any may be NULL).  Synchronous. */
+int lbm_run_host(lbm_ctx *ctx, const float *f_pre_host, int n, lbm_collision kind,
+                 const lbm_weights *w, float *rho_host, float *ux_host, float *uy_host);
+
+/* Static description of an error code. */
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,74 @@
+// kernels.h -- internal launcher interface between the C ABI (lbm_api.cu)
+// and the kernel translation units.  Not installed; not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace lbm {
+
+// Grid description shared by all launchers.
+struct Grid {
+  int nx, ny, batch;
+  size_t plane() const { return (size_t)nx * ny; }
+  size_t nodes() const { return plane() * batch; }
+  size_t state_floats() const { return 9 * nodes(); }
+};
+
+// Per-launch collision parameters (FP32 copies of lbm_params).
+struct CollideParams {
+  float tau, omega;      // tau, 1/tau
+  float tau0_sq;         // tau^2 (Smagorinsky)
+  float smag_c18;        // 18 (C_s Delta)^2 (Smagorinsky)
+  const float *force;    // per-row F_x(y), ny floats (device), or nullptr
+};
+
+// FP32 weights packed in the library's order (device pointers).
+struct MlpF32 {
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+};
+
+// step_fp32.cu ---------------------------------------------------------------
+cudaError_t launch_step_bgk(const Grid &g, const float *in, float *out, const CollideParams &p,
+                            int *flag, cudaStream_t s);
+cudaError_t launch_step_smag(const Grid &g, const float *in, float *out, const CollideParams &p,
+                             int *flag, cudaStream_t s);
+cudaError_t launch_set_state(const Grid &g, const float *f_pre, float *state, cudaStream_t s);
+cudaError_t launch_get_state(const Grid &g, const float *state, float *f_pre, cudaStream_t s);
+cudaError_t launch_init_equilibrium(const Grid &g, const float *rho, const float *ux,
+                                    const float *uy, float *state, cudaStream_t s);
+cudaError_t launch_moments(const Grid &g, const float *state, float *rho, float *ux, float *uy,
+                           cudaStream_t s);
+cudaError_t launch_box_filter(const Grid &g, const float *state, int cg, float *f_coarse,
+                              cudaStream_t s);
+// Loss: per-block partial sums into `partials` (>= loss_partials(g) floats),
+// then a single-block fixed-order sum into loss[0].
+int loss_partials(const Grid &g);
+cudaError_t launch_velocity_loss(const Grid &g, const float *state, const float *utx,
+                                 const float *uty, float *partials, float *loss, float *dL_df,
+                                 cudaStream_t s);
+// push (transpose of the pull) of an adjoint field: out_i(x) = in_i(x + c_i)
+cudaError_t launch_push(const Grid &g, const float *in, float *out, cudaStream_t s);
+// pull of an adjoint field: out_i(x) = in_i(x - c_i)
+cudaError_t launch_pull(const Grid &g, const float *in, float *out, cudaStream_t s);
+
+// mlp_f32.cu -------------------------------------------------------------------
+cudaError_t launch_step_mlp_f32(const Grid &g, const float *in, float *out,
+                                const CollideParams &p, const MlpF32 &w, int *flag,
+                                cudaStream_t s);
+
+// mlp_bf16.cu ------------------------------------------------------------------
+// weights: FP32 (dtype 0) or BF16 (dtype 1), same packed row-major layout.
+cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
+                                 const CollideParams &p, const void *const wptr[6], int dtype,
+                                 int *flag, int *timeout_flag, cudaStream_t s);
+
+// adjoint.cu -------------------------------------------------------------------
+// Number of CTAs (= rows of per-CTA dW partials) of the adjoint step.
+int adjoint_blocks(const Grid &g, int sms);
+size_t adjoint_smem_bytes();
+cudaError_t launch_adjoint_step(const Grid &g, const float *state_n, const float *lam_next,
+                                float *lam_out, const CollideParams &p, const MlpF32 &w,
+                                float *dw_partials, int rows, int accumulate, cudaStream_t s);
+cudaError_t launch_reduce_dw(const float *dw_partials, int rows, float *dW, cudaStream_t s);
+
+}  // namespace lbm

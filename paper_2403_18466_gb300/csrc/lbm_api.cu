@@ -1,0 +1,361 @@
+// lbm_api.cu -- the C ABI declared in include/lbm.h: argument checking,
+// the context (stream, ping-pong state buffers, small scratch), and the
+// launch sequences of every entry point.  No arithmetic of the method lives
+// here; it is all in the kernels.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "kernels.h"
+#include "lattice.cuh"
+
+using lbm::CollideParams;
+using lbm::Grid;
+using lbm::MlpF32;
+
+struct lbm_ctx {
+  lbm_params p;
+  Grid g;
+  float *buf[2];
+  int cur;
+  cudaStream_t stream;
+  int device;
+  int sms;
+  CollideParams cp;
+  // scratch (library-owned, device)
+  int *d_flag;          // [0] unstable, [1] device wait timeout
+  float *d_force;       // ny floats, or nullptr
+  float *d_loss_part;   // lbm::loss_partials(g) floats
+  float *d_dw_part;     // dw_rows * NPARAMS floats (allocated on first use)
+  int dw_rows;
+  // last lbm_forward_record
+  int rec_n, rec_k;
+  const void *rec_ws;
+};
+
+namespace {
+
+#define CUDA_TRY(expr)                          \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) return LBM_ERR_CUDA; \
+  } while (0)
+
+bool bad_params(const lbm_params *p) {
+  if (!p) return true;
+  if (p->nx < 1 || p->ny < 1 || p->batch < 1) return true;
+  if ((long long)p->nx * p->ny * p->batch * 9 > (1LL << 40)) return true;
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return true;
+  if (!(p->smag_cs >= 0.0) || !(p->smag_delta > 0.0)) return true;
+  if (!std::isfinite(p->force_amp) || p->flags != 0) return true;
+  return false;
+}
+
+int check_weights(lbm_collision kind, const lbm_weights *w) {
+  if (kind == LBM_BGK || kind == LBM_SMAG) return LBM_OK;
+  if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3) return LBM_ERR_ARG;
+  if (w->dtype != 0 && w->dtype != 1) return LBM_ERR_ARG;
+  if (kind == LBM_MLP_F32 && w->dtype != 0) return LBM_ERR_UNSUPPORTED;
+  return LBM_OK;
+}
+
+MlpF32 f32_view(const lbm_weights *w) {
+  MlpF32 m;
+  m.w1 = static_cast<const float *>(w->w1);
+  m.b1 = static_cast<const float *>(w->b1);
+  m.w2 = static_cast<const float *>(w->w2);
+  m.b2 = static_cast<const float *>(w->b2);
+  m.w3 = static_cast<const float *>(w->w3);
+  m.b3 = static_cast<const float *>(w->b3);
+  return m;
+}
+
+// One step from `in` to `out` with the given collision.
+cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind,
+                     const lbm_weights *w) {
+  switch (kind) {
+    case LBM_BGK: return lbm::launch_step_bgk(c->g, in, out, c->cp, c->d_flag, c->stream);
+    case LBM_SMAG: return lbm::launch_step_smag(c->g, in, out, c->cp, c->d_flag, c->stream);
+    case LBM_MLP_F32:
+      return lbm::launch_step_mlp_f32(c->g, in, out, c->cp, f32_view(w), c->d_flag, c->stream);
+    case LBM_MLP_BF16: {
+      const void *wp[6] = {w->w1, w->b1, w->w2, w->b2, w->w3, w->b3};
+      return lbm::launch_step_mlp_bf16(c->g, in, out, c->cp, wp, w->dtype, c->d_flag,
+                                       c->d_flag + 1, c->stream);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+int ensure_dw_partials(lbm_ctx *c) {
+  if (c->d_dw_part) return LBM_OK;
+  c->dw_rows = lbm::adjoint_blocks(c->g, c->sms);
+  CUDA_TRY(cudaMalloc(&c->d_dw_part, (size_t)c->dw_rows * lbm::NPARAMS * sizeof(float)));
+  return LBM_OK;
+}
+
+size_t state_bytes(const lbm_params *p) {
+  return (size_t)9 * p->nx * p->ny * p->batch * sizeof(float);
+}
+
+int n_checkpoints(int n, int k) { return n == 0 ? 1 : (n + k - 1) / k; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_UNSUPPORTED: return "unsupported by this build";
+    case LBM_ERR_UNSTABLE: return "unstable: |u| >= 0.4 or non-finite velocity";
+    case LBM_ERR_TIMEOUT: return "a bounded device wait gave up";
+  }
+  return "unknown error";
+}
+
+int lbm_init(lbm_ctx **out, const lbm_params *p, float *f_buf0, float *f_buf1,
+             void *cuda_stream) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (bad_params(p) || !f_buf0 || !f_buf1 || f_buf0 == f_buf1) return LBM_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(f_buf0) | reinterpret_cast<uintptr_t>(f_buf1)) & 15)
+    return LBM_ERR_ARG;  // 16-byte alignment for the vector loads
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_ARG;
+  c->p = *p;
+  c->g = Grid{p->nx, p->ny, p->batch};
+  c->buf[0] = f_buf0;
+  c->buf[1] = f_buf1;
+  c->cur = 0;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return LBM_ERR_CUDA;
+  }
+  c->cp.tau = (float)p->tau;
+  c->cp.omega = (float)(1.0 / p->tau);
+  c->cp.tau0_sq = (float)(p->tau * p->tau);
+  c->cp.smag_c18 = (float)(18.0 * (p->smag_cs * p->smag_delta) * (p->smag_cs * p->smag_delta));
+  c->cp.force = nullptr;
+  int rc = LBM_OK;
+  if (cudaMalloc(&c->d_flag, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_flag, 0, 2 * sizeof(int)) != cudaSuccess)
+    rc = LBM_ERR_CUDA;
+  if (rc == LBM_OK && p->force_amp != 0.0) {
+    // F_x(y) = F0 sin(2 pi m y / ny), evaluated in double on the host
+    float *h = static_cast<float *>(std::malloc(sizeof(float) * p->ny));
+    if (!h) rc = LBM_ERR_ARG;
+    for (int y = 0; rc == LBM_OK && y < p->ny; ++y)
+      h[y] = (float)(p->force_amp * std::sin(2.0 * M_PI * (double)p->force_mode * y / p->ny));
+    if (rc == LBM_OK && (cudaMalloc(&c->d_force, sizeof(float) * p->ny) != cudaSuccess ||
+                         cudaMemcpy(c->d_force, h, sizeof(float) * p->ny,
+                                    cudaMemcpyHostToDevice) != cudaSuccess))
+      rc = LBM_ERR_CUDA;
+    std::free(h);
+    c->cp.force = c->d_force;
+  }
+  if (rc == LBM_OK &&
+      cudaMalloc(&c->d_loss_part, sizeof(float) * lbm::loss_partials(c->g)) != cudaSuccess)
+    rc = LBM_ERR_CUDA;
+  if (rc != LBM_OK) {
+    lbm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(c->d_flag);
+  cudaFree(c->d_force);
+  cudaFree(c->d_loss_part);
+  cudaFree(c->d_dw_part);
+  delete c;
+}
+
+float *lbm_state_buffer(lbm_ctx *c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_set_state(lbm_ctx *c, const float *f_pre) {
+  if (!c || !f_pre) return LBM_ERR_ARG;
+  if (f_pre == c->buf[c->cur]) return LBM_ERR_ARG;  // the anti-stream needs a separate source
+  CUDA_TRY(lbm::launch_set_state(c->g, f_pre, c->buf[c->cur], c->stream));
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx *c, float *f_pre) {
+  if (!c || !f_pre || f_pre == c->buf[c->cur]) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_get_state(c->g, c->buf[c->cur], f_pre, c->stream));
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_ctx *c, const float *rho, const float *ux, const float *uy) {
+  if (!c || !rho || !ux || !uy) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_init_equilibrium(c->g, rho, ux, uy, c->buf[c->cur], c->stream));
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int n, lbm_collision kind, const lbm_weights *w) {
+  if (!c || n < 0) return LBM_ERR_ARG;
+  if (kind < LBM_BGK || kind > LBM_MLP_F32) return LBM_ERR_ARG;
+  const int wc = check_weights(kind, w);
+  if (wc != LBM_OK) return wc;
+  for (int s = 0; s < n; ++s) {
+    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w));
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, float *rho, float *ux, float *uy) {
+  if (!c) return LBM_ERR_ARG;
+  if (!rho && !ux && !uy) return LBM_OK;
+  CUDA_TRY(lbm::launch_moments(c->g, c->buf[c->cur], rho, ux, uy, c->stream));
+  return LBM_OK;
+}
+
+int lbm_status(lbm_ctx *c) {
+  if (!c) return LBM_ERR_ARG;
+  int h[2] = {0, 0};
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpy(h, c->d_flag, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[1]) return LBM_ERR_TIMEOUT;
+  if (h[0]) return LBM_ERR_UNSTABLE;
+  return LBM_OK;
+}
+
+int lbm_clear_status(lbm_ctx *c) {
+  if (!c) return LBM_ERR_ARG;
+  CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, 2 * sizeof(int), c->stream));
+  return LBM_OK;
+}
+
+int lbm_velocity_loss(lbm_ctx *c, const float *utx, const float *uty, float *loss,
+                      float *dL_df) {
+  if (!c || !utx || !uty || !loss) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_velocity_loss(c->g, c->buf[c->cur], utx, uty, c->d_loss_part, loss, dL_df,
+                                     c->stream));
+  return LBM_OK;
+}
+
+size_t lbm_record_bytes(const lbm_params *p, int n, int k) {
+  if (bad_params(p) || n < 0 || k < 1) return 0;
+  // checkpoints + (k - 1) recomputed states of one segment + 2 adjoint buffers
+  const size_t states = (size_t)n_checkpoints(n, k) + (size_t)(k - 1) + 2;
+  return states * state_bytes(p);
+}
+
+int lbm_forward_record(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
+                       size_t ws_bytes) {
+  if (!c || n < 0 || k < 1 || !ws) return LBM_ERR_ARG;
+  if (check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
+  if (ws_bytes < lbm_record_bytes(&c->p, n, k)) return LBM_ERR_ARG;
+  const size_t sb = state_bytes(&c->p);
+  char *base = static_cast<char *>(ws);
+  for (int s = 0; s < n; ++s) {
+    if (s % k == 0)
+      CUDA_TRY(cudaMemcpyAsync(base + (size_t)(s / k) * sb, c->buf[c->cur], sb,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], LBM_MLP_F32, w));
+    c->cur ^= 1;
+  }
+  if (n == 0)
+    CUDA_TRY(cudaMemcpyAsync(base, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
+  c->rec_n = n;
+  c->rec_k = k;
+  c->rec_ws = ws;
+  return LBM_OK;
+}
+
+int lbm_backward(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w, void *ws,
+                 size_t ws_bytes, float *dW, float *dL_df0) {
+  if (!c || !dL_df_final || !ws || !dW) return LBM_ERR_ARG;
+  if (check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
+  if (ws != c->rec_ws) return LBM_ERR_ARG;  // needs the workspace of the last record
+  const int n = c->rec_n, k = c->rec_k;
+  if (ws_bytes < lbm_record_bytes(&c->p, n, k)) return LBM_ERR_ARG;
+  int rc = ensure_dw_partials(c);
+  if (rc != LBM_OK) return rc;
+  const size_t sb = state_bytes(&c->p);
+  char *base = static_cast<char *>(ws);
+  const int nck = n_checkpoints(n, k);
+  float *seg = reinterpret_cast<float *>(base + (size_t)nck * sb);  // k - 1 states
+  float *lam[2] = {reinterpret_cast<float *>(base + (size_t)(nck + k - 1) * sb),
+                   reinterpret_cast<float *>(base + (size_t)(nck + k) * sb)};
+  const size_t sf = sb / sizeof(float);
+  const MlpF32 wf = f32_view(w);
+  // lam = dL/d(stored state g^n): the transpose of the final pull is a push
+  CUDA_TRY(lbm::launch_push(c->g, dL_df_final, lam[0], c->stream));
+  int cur = 0;
+  bool first = true;
+  for (int s0 = ((n - 1) / k) * k; n > 0 && s0 >= 0; s0 -= k) {
+    const float *ck = reinterpret_cast<const float *>(base + (size_t)(s0 / k) * sb);
+    const int len = (s0 + k <= n) ? k : n - s0;
+    // recompute g^{s0+1} .. g^{s0+len-1} into seg[0 .. len-2]
+    for (int j = 1; j < len; ++j) {
+      const float *in = j == 1 ? ck : seg + (size_t)(j - 2) * sf;
+      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, LBM_MLP_F32, w));
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      const float *gs = j == 0 ? ck : seg + (size_t)(j - 1) * sf;
+      CUDA_TRY(lbm::launch_adjoint_step(c->g, gs, lam[cur], lam[cur ^ 1], c->cp, wf,
+                                        c->d_dw_part, c->dw_rows, first ? 0 : 1, c->stream));
+      first = false;
+      cur ^= 1;
+    }
+  }
+  if (first) {
+    CUDA_TRY(cudaMemsetAsync(dW, 0, sizeof(float) * lbm::NPARAMS, c->stream));
+  } else {
+    CUDA_TRY(lbm::launch_reduce_dw(c->d_dw_part, c->dw_rows, dW, c->stream));
+  }
+  // dL/df_pre(0) = pull(lam^0): g^0 was the push of f_pre(0)
+  if (dL_df0) CUDA_TRY(lbm::launch_pull(c->g, lam[cur], dL_df0, c->stream));
+  return LBM_OK;
+}
+
+int lbm_box_filter(lbm_ctx *c, int cg, float *f_coarse) {
+  if (!c || !f_coarse || cg < 1) return LBM_ERR_ARG;
+  if (c->g.nx % cg || c->g.ny % cg) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_box_filter(c->g, c->buf[c->cur], cg, f_coarse, c->stream));
+  return LBM_OK;
+}
+
+int lbm_run_host(lbm_ctx *c, const float *f_pre_host, int n, lbm_collision kind,
+                 const lbm_weights *w, float *rho_host, float *ux_host, float *uy_host) {
+  if (!c || !f_pre_host || n < 0) return LBM_ERR_ARG;
+  if (kind < LBM_BGK || kind > LBM_MLP_F32) return LBM_ERR_ARG;
+  const int wc = check_weights(kind, w);
+  if (wc != LBM_OK) return wc;
+  const size_t sb = state_bytes(&c->p);
+  // the non-current buffer stages the input, then the output fields
+  float *stage = c->buf[c->cur ^ 1];
+  CUDA_TRY(cudaMemcpyAsync(stage, f_pre_host, sb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(lbm::launch_set_state(c->g, stage, c->buf[c->cur], c->stream));
+  int rc = lbm_step(c, n, kind, w);
+  if (rc != LBM_OK) return rc;
+  const size_t nn = c->g.nodes();
+  float *out = c->buf[c->cur ^ 1];
+  CUDA_TRY(lbm::launch_moments(c->g, c->buf[c->cur], out, out + nn, out + 2 * nn, c->stream));
+  if (rho_host)
+    CUDA_TRY(cudaMemcpyAsync(rho_host, out, nn * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (ux_host)
+    CUDA_TRY(cudaMemcpyAsync(ux_host, out + nn, nn * sizeof(float), cudaMemcpyDeviceToHost,
+                             c->stream));
+  if (uy_host)
+    CUDA_TRY(cudaMemcpyAsync(uy_host, out + 2 * nn, nn * sizeof(float), cudaMemcpyDeviceToHost,
+                             c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -80,8 +80,13 @@ def mlp_nparams(h: int = HIDDEN) -> int:
     return h * 9 + h + h * h + h + 9 * h + 9
 
 
-def xavier_mlp(seed: int, h: int = HIDDEN, bias_scale: float = 0.0, gain: float = 1.0):
-    """Packed float64 weights of the 9 -> h -> h -> 9 network (Glorot uniform)."""
+def xavier_mlp(seed: int, h: int = HIDDEN, bias_scale: float = 0.0, gain: float = 1.0,
+               out_scale: float = 1.0):
+    """Packed float64 weights of the 9 -> h -> h -> 9 network (Glorot uniform).
+
+    ``gain`` scales the two hidden layers' bounds, ``out_scale`` multiplies the
+    output layer (W3 and b3), so that a strongly non-linear network can still
+    produce a correction of the size of the non-equilibrium populations."""
     rng = np.random.Generator(np.random.PCG64(seed))
 
     def glorot(fan_out, fan_in):
@@ -90,8 +95,9 @@ def xavier_mlp(seed: int, h: int = HIDDEN, bias_scale: float = 0.0, gain: float 
 
     W1 = glorot(h, 9)
     W2 = glorot(h, h)
-    W3 = glorot(9, h)
+    W3 = glorot(9, h) / gain * out_scale
     b1, b2, b3 = (bias_scale * rng.uniform(-1.0, 1.0, size=m) for m in (h, h, 9))
+    b3 = b3 * out_scale
     return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
 
 

@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every entry
+point that include/lbm.h declares; host-side argument checks that run before
+any CUDA call (no compute without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_18466_gb300 import build, lbm
+    build.build()
+    return lbm.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"lbm_init", "lbm_step", "lbm_moments", "lbm_backward"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_host_side_argument_errors(lib):
+    from paper_2403_18466_gb300 import lbm
+    ctx = C.c_void_p()
+    p = lbm.make_params(16, 16, 1, tau=0.6)
+    assert lib.lbm_init(C.byref(ctx), None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_init(None, C.byref(p), None, None, None) == lbm.LBM_ERR_ARG
+    bad = lbm.make_params(16, 16, 1, tau=0.5)  # tau must exceed 1/2
+    assert lib.lbm_init(C.byref(ctx), C.byref(bad), C.c_void_p(256), C.c_void_p(512), None) \
+        == lbm.LBM_ERR_ARG
+    bad = lbm.make_params(0, 16, 1, tau=0.6)
+    assert lib.lbm_init(C.byref(ctx), C.byref(bad), C.c_void_p(256), C.c_void_p(512), None) \
+        == lbm.LBM_ERR_ARG
+    assert lib.lbm_step(None, 1, 0, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_moments(None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_status(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_state_buffer(None) is None
+    lib.lbm_destroy(None)
+
+
+def test_record_bytes_and_strerror(lib):
+    from paper_2403_18466_gb300 import lbm
+    p = lbm.make_params(256, 256, 32, tau=0.500375)
+    sb = 9 * 256 * 256 * 32 * 4
+    # 16 steps, checkpoint every 4: 4 checkpoints + 3 recomputed + 2 adjoint buffers
+    assert lbm.lbm_record_bytes(p, 16, 4) == 9 * sb
+    assert lbm.lbm_record_bytes(p, 16, 0) == 0
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lbm.lbm_strerror(code)
+    assert lbm.lbm_strerror(-99) == "unknown error"

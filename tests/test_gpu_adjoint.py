@@ -1,0 +1,75 @@
+"""GPU parity of the hand-written adjoint (unrolled training, SI section 2)
+against the oracle's reverse mode, which is itself pinned by central finite
+differences (tests/test_oracle_adjoint.py).
+
+Tolerance: 1e-4 relative (infinity norm) on dL/dtheta and on dL/df0, from
+FP32 accumulation over the unroll; the loss to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_18466_gb300 import inputs
+from gpu_helpers import population_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2403_18466_gb300 import lbm as m
+    m.load()
+    return m
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=DEV)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("nx,ny,B,steps,ck", [(24, 16, 2, 5, 2), (160, 12, 1, 4, 4), (32, 32, 1, 3, 1)])
+def test_backward_matches_oracle(lbm, nx, ny, B, steps, ck):
+    tau, F0, m = 0.6, 1e-4, 1
+    theta = inputs.xavier_mlp(7, bias_scale=0.3, gain=3.0, out_scale=0.01)
+    th32 = theta.astype(np.float32).astype(np.float64)
+    f0 = population_field(B, ny, nx, seed=61, neq=0.05)
+    utx = inputs.noise((B, ny, nx), 62, 0.03).astype(np.float32)
+    uty = inputs.noise((B, ny, nx), 63, 0.03).astype(np.float32)
+
+    lat = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
+    th = _dev(theta)
+    w = lbm.weights_struct(th)
+    lat.set_state(_dev(f0))
+    ws = torch.empty(lat.record_bytes(steps, ck) // 4, dtype=torch.float32, device=DEV)
+    lat.forward_record(steps, ck, w, ws)
+    loss, dL_df = lat.velocity_loss(_dev(utx), _dev(uty))
+    dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=DEV)
+    dF0 = torch.empty_like(dL_df)
+    lat.backward(dL_df, w, ws, dW, dF0)
+    assert lat.status() == lbm.LBM_OK
+
+    prm = oracle.params(tau, force_amp=F0, force_mode=m)
+    g0 = oracle.stream_push(f0.astype(np.float64))
+    L, dth, dg0 = oracle.unroll_grad(g0, steps, prm, th32, utx.astype(np.float64),
+                                     uty.astype(np.float64))
+    assert abs(float(loss.item()) / L - 1) <= 1e-5
+    dWg = _np(dW)
+    assert np.abs(dWg - dth).max() <= 1e-4 * np.abs(dth).max()
+    df0 = oracle.stream_pull(dg0)
+    assert np.abs(_np(dF0) - df0).max() <= 1e-4 * np.abs(df0).max()
+    # the forward that was recorded is the plain learned-collision run
+    lat2 = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
+    lat2.set_state(_dev(f0))
+    lat2.step(steps, "mlp_f32", w)
+    assert torch.equal(lat2.get_state(), lat.get_state())
+    # deterministic: a second backward gives the same bits
+    dW2 = torch.empty_like(dW)
+    lat.backward(dL_df, w, ws, dW2, None)
+    assert torch.equal(dW, dW2)

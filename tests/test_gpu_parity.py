@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (from the FP32 arithmetic of the kernels):
+  * FP32 BGK populations after 1000 steps (64^2 Taylor-Green): 1e-5 relative;
+  * one FP32 step of every kind, populations: 1e-5 of each weight w_i
+    (max |df_i| / w_i; a learned correction can take a population near zero,
+    where a plain relative error is ill conditioned);
+  * FP32 learned collision, velocity per step: 1e-5 relative;
+  * conserved moments: total mass drift <= 1e-6 relative over a run;
+  * data-movement kernels (state in/out, moments, filter): FP32 rounding.
+Sizes span several tiles of every kernel plus a ragged tail; the scalar
+kernel (nx % 4 != 0) and the vector kernel (nx % 4 == 0) are both covered.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_18466_gb300 import inputs
+from gpu_helpers import population_field, rel_pop_err, rel_vel_err, weighted_pop_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2403_18466_gb300 import lbm as m
+    m.load()
+    return m
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=DEV)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def test_taylor_green_bgk_1000_steps(lbm):
+    n, tau, u0 = 64, 0.6, 0.01
+    k = 2 * np.pi / n
+    rho, ux, uy = inputs.taylor_green(n, u0, k)
+    lat = lbm.Lattice(n, n, 1, tau=tau, device=DEV)
+    lat.init_equilibrium(_dev(rho[None]), _dev(ux[None]), _dev(uy[None]))
+    f0 = lat.get_state()
+    g = oracle.stream_push(_np(f0))  # the oracle starts from the GPU's FP32 input
+    mass0 = float(_np(f0).sum())
+    lat.step(1000, "bgk")
+    g = oracle.run(oracle.BGK, g, 1000, oracle.params(tau))
+    fg = _np(lat.get_state())
+    assert lat.status() == lbm.LBM_OK
+    err = rel_pop_err(fg, oracle.stream_pull(g))
+    assert err <= 1e-5, err
+    assert abs(fg.sum() / mass0 - 1.0) <= 1e-6
+    # the decay itself (the physics), from the GPU run
+    _, vx, _ = lat.moments()
+    amp = float(np.sum(_np(vx)[0] * ux) / np.sum(ux * ux) * u0)
+    nu = (tau - 0.5) / 3
+    assert abs(amp / (u0 * np.exp(-2 * nu * k * k * 1000)) - 1) < 0.02
+
+
+SHAPES = [(64, 64, 1), (37, 29, 2), (132, 40, 1), (4, 3, 1), (1, 1, 1), (1028, 9, 1)]
+
+
+@pytest.mark.parametrize("nx,ny,B", SHAPES)
+@pytest.mark.parametrize("kind", ["bgk", "smag", "mlp_f32"])
+def test_one_step_parity(lbm, kind, nx, ny, B):
+    tau = 0.52 if kind == "smag" else 0.6
+    prm = oracle.params(tau, smag_cs=0.1, force_amp=1e-4, force_mode=2)
+    theta = inputs.xavier_mlp(5, bias_scale=0.3, gain=3.0, out_scale=0.02)
+    f = population_field(B, ny, nx, seed=nx * 7 + ny)
+    lat = lbm.Lattice(nx, ny, B, tau=tau, smag_cs=0.1, force_amp=1e-4, force_mode=2, device=DEV)
+    th = torch.tensor(theta, dtype=torch.float32, device=DEV)
+    w = lbm.weights_struct(th)
+    lat.set_state(_dev(f))
+    okind = {"bgk": oracle.BGK, "smag": oracle.SMAG, "mlp_f32": oracle.MLP}[kind]
+    g = oracle.stream_push(f.astype(np.float64))
+    for _ in range(3):
+        lat.step(1, kind, w)
+        g = oracle.step(okind, g, prm, theta.astype(np.float32).astype(np.float64))
+        fg = _np(lat.get_state())
+        fr = oracle.stream_pull(g)
+        assert weighted_pop_err(fg, fr) <= 1e-5
+        _, gx, gy = (_np(t) for t in lat.moments())
+        _, rx, ry = oracle.moments(fr)
+        assert rel_vel_err(gx, gy, rx, ry) <= 1e-5
+    assert lat.status() == lbm.LBM_OK
+
+
+def test_state_roundtrip_equilibrium_and_moments(lbm):
+    B, ny, nx = 2, 33, 20
+    f = population_field(B, ny, nx, seed=3)
+    lat = lbm.Lattice(nx, ny, B, device=DEV)
+    lat.set_state(_dev(f))
+    back = _np(lat.get_state())
+    assert np.max(np.abs(back - f) / f) <= 2 * 2.0 ** -24 * 4  # (f - w) + w in FP32
+    r, vx, vy = (_np(t) for t in lat.moments())
+    rr, rx, ry = oracle.moments(f.astype(np.float64))
+    assert np.max(np.abs(r - rr) / rr) <= 1e-6
+    assert rel_vel_err(vx, vy, rx, ry) <= 1e-5
+    rho = 1.0 + inputs.noise((B, ny, nx), 4, 0.02)
+    ux, uy = inputs.noise((B, ny, nx), 5, 0.05), inputs.noise((B, ny, nx), 6, 0.05)
+    lat.init_equilibrium(_dev(rho), _dev(ux), _dev(uy))
+    fe = _np(lat.get_state())
+    ref = oracle.equilibrium_field(rho.astype(np.float32).astype(np.float64),
+                                   ux.astype(np.float32).astype(np.float64),
+                                   uy.astype(np.float32).astype(np.float64))
+    assert rel_pop_err(fe, ref) <= 1e-6
+
+
+def test_zero_steps_is_identity(lbm):
+    f = population_field(1, 16, 12, seed=9)
+    lat = lbm.Lattice(12, 16, 1, device=DEV)
+    lat.set_state(_dev(f))
+    a = _np(lat.get_state())
+    lat.step(0, "bgk")
+    assert np.array_equal(_np(lat.get_state()), a)
+
+
+@pytest.mark.parametrize("kind", ["bgk", "smag", "mlp_f32"])
+def test_global_conservation_over_run(lbm, kind):
+    B, n = 1, 96
+    f = population_field(B, n, n, seed=21)
+    lat = lbm.Lattice(n, n, B, tau=0.55, smag_cs=0.1, force_amp=1e-5, force_mode=1, device=DEV)
+    th = torch.tensor(inputs.xavier_mlp(2, bias_scale=0.3, gain=2.0, out_scale=0.02), dtype=torch.float32, device=DEV)
+    w = lbm.weights_struct(th)
+    lat.set_state(_dev(f))
+    m0 = float(_np(lat.get_state()).sum())
+    lat.step(200, kind, w)
+    m1 = float(_np(lat.get_state()).sum())
+    assert abs(m1 / m0 - 1) <= 1e-6
+    # one more step: momentum changes by sum_y F(y) * nx = 0 up to rounding
+    fa = _np(lat.get_state())
+    lat.step(1, kind, w)
+    fb = _np(lat.get_state())
+    cx, cy, _ = oracle.lattice()
+    jx = [np.einsum("biyx,i->", a, cx) for a in (fa, fb)]
+    assert abs(jx[1] - jx[0]) <= 1e-6 * n * n * 1e-2
+
+
+def test_box_filter_parity(lbm):
+    B, ny, nx, cg = 2, 48, 64, 8
+    f = population_field(B, ny, nx, seed=31)
+    lat = lbm.Lattice(nx, ny, B, device=DEV)
+    lat.set_state(_dev(f))
+    fc = _np(lat.box_filter(cg))
+    fpre = _np(lat.get_state())
+    ref = oracle.box_filter(fpre, cg)
+    assert rel_pop_err(fc, ref) <= 1e-6
+
+
+def test_velocity_loss_parity(lbm):
+    B, ny, nx = 2, 24, 40
+    f = population_field(B, ny, nx, seed=41)
+    utx, uty = inputs.noise((B, ny, nx), 42, 0.03), inputs.noise((B, ny, nx), 43, 0.03)
+    lat = lbm.Lattice(nx, ny, B, device=DEV)
+    lat.set_state(_dev(f))
+    loss, grad = lat.velocity_loss(_dev(utx), _dev(uty))
+    fpre = _np(lat.get_state())
+    u32 = (utx.astype(np.float32).astype(np.float64), uty.astype(np.float32).astype(np.float64))
+    Lr = oracle.velocity_loss(fpre, *u32)
+    Gr = oracle.velocity_loss_grad(fpre, *u32)
+    assert abs(float(loss.item()) / Lr - 1) <= 1e-5
+    assert np.abs(_np(grad) - Gr).max() <= 1e-5 * np.abs(Gr).max()
+    # deterministic reduction
+    l2, _ = lat.velocity_loss(_dev(utx), _dev(uty), want_grad=False)
+    assert float(l2.item()) == float(loss.item())
+
+
+def test_unstable_state_sets_status(lbm):
+    n = 16
+    rho = np.ones((1, n, n))
+    ux = np.full((1, n, n), 0.5)  # |u| = 0.5 > 0.4
+    lat = lbm.Lattice(n, n, 1, device=DEV)
+    lat.init_equilibrium(_dev(rho), _dev(ux), _dev(np.zeros_like(ux)))
+    lat.step(1, "bgk")
+    assert lat.status() == lbm.LBM_ERR_UNSTABLE
+    lat.clear_status()
+    assert lat.status() == lbm.LBM_OK
+
+
+def test_run_host_matches_device_path(lbm):
+    B, ny, nx = 1, 40, 64
+    f = population_field(B, ny, nx, seed=51)
+    th = torch.tensor(inputs.xavier_mlp(2, bias_scale=0.3, gain=2.0, out_scale=0.02), dtype=torch.float32, device=DEV)
+    w = lbm.weights_struct(th)
+    lat = lbm.Lattice(nx, ny, B, device=DEV)
+    lat.set_state(_dev(f))
+    lat.step(5, "mlp_f32", w)
+    r, vx, vy = (_np(t) for t in lat.moments())
+    host = torch.tensor(f).pin_memory()
+    outs = [torch.empty((B, ny, nx), dtype=torch.float32).pin_memory() for _ in range(3)]
+    lat2 = lbm.Lattice(nx, ny, B, device=DEV)
+    lat2.run_host(host, 5, "mlp_f32", w, *outs)
+    for a, b in zip((r, vx, vy), outs):
+        assert np.array_equal(a, b.double().numpy())
+
+
+def test_argument_errors(lbm):
+    lat = lbm.Lattice(8, 8, 1, device=DEV)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(-1, "bgk")
+    assert e.value.code == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(1, "mlp_f32", None)
+    assert e.value.code == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        lat.box_filter(3)
+    assert e.value.code == lbm.LBM_ERR_ARG
