@@ -1,11 +1,349 @@
-// mlp_bf16.cu -- placeholder until the tensor-core learned collision lands.
+// mlp_bf16.cu -- fused pull-stream + learned collision with the MLP on the
+// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+// tensor memory).  Populations, moments, equilibrium, projection and the
+// BGK/forcing update stay in FP32.
+//
+// Per node (Eq. S10-S12 with the network of this library):
+//   x = (f - feq)/rho;  h1 = tanh(W1 x + b1);  h2 = tanh(W2 h1 + b2);  o = W3 h2 + b3
+//   f' = f + (feq - f)/tau + (rho/tau) P o + f_ext,   P = mass/momentum projection
+//
+// Work decomposition.  A tile is 128 consecutive nodes of one row; one
+// warpgroup (128 threads, thread r = node r = tensor-memory lane r) owns a
+// tile at a time, and a CTA holds two warpgroups that walk disjoint tile
+// sequences (persistent, grid = 2 CTAs per SM).  Each layer is one GEMM with
+// M = 128 nodes:
+//   layer 1: [128 x 16] x [16 x 64]   K = 9 inputs + a constant-1 column (b1) + 6 zeros
+//   layer 2: [128 x 80] x [80 x 64]   K = 64 hidden + constant-1 column (b2) + 15 zeros
+//   layer 3: [128 x 80] x [80 x 16]   N = 9 outputs + 7 zero columns, b3 via the 1-column
+// so the biases ride on the MMA.  Operands live in shared memory in the
+// canonical K-major no-swizzle layout (umma.cuh); the accumulators live in
+// tensor memory (D1: 64 columns, reused by D3; D2: 64 columns).  Between
+// layers each thread reads its own row back with tcgen05.ld, applies tanh on
+// packed bf16 pairs and writes the next operand row.  The populations of the
+// next tile are loaded while the current tile's three GEMMs run.
+//
+// Synchronisation per warpgroup: operand rows written by all 128 threads
+// -> fence.proxy.async + named barrier -> one thread issues the MMAs and
+// commits them to the warpgroup's mbarrier -> all threads wait on it (bounded
+// wait; on time-out the kernel sets the timeout flag, drains, frees tensor
+// memory and returns).
+#include <cuda_bf16.h>
+
 #include "kernels.h"
+#include "lattice.cuh"
+#include "umma.cuh"
 
 namespace lbm {
+namespace {
 
-cudaError_t launch_step_mlp_bf16(const Grid &, const float *, float *, const CollideParams &,
-                                 const void *const[6], int, int *, int *, cudaStream_t) {
-  return cudaErrorNotSupported;
+using namespace umma;
+
+constexpr int WG_THREADS = 128;
+constexpr int THREADS = 2 * WG_THREADS;
+constexpr int K1 = 16, K2 = 80;  // padded K of layer 1 and of layers 2/3
+constexpr uint32_t TMEM_COLS = 256;  // per CTA: 128 per warpgroup
+constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
+
+struct __align__(1024) Smem {
+  unsigned char w1[HIDDEN * K1 * 2];   // B of layer 1: [64 x 16]
+  unsigned char w2[HIDDEN * K2 * 2];   // B of layer 2: [64 x 80]
+  unsigned char w3[16 * K2 * 2];       // B of layer 3: [16 x 80]
+  unsigned char a1[2][128 * K1 * 2];   // A of layer 1, per warpgroup
+  unsigned char a23[2][128 * K2 * 2];  // A of layers 2 and 3, per warpgroup
+  unsigned long long bar[2];
+  uint32_t taddr;
+};
+// Shared memory requested per CTA: padded so that at most two CTAs share an
+// SM (each allocates 256 of the 512 tensor-memory columns).
+constexpr size_t SMEM_BYTES = 84 * 1024;
+static_assert(sizeof(Smem) + 1024 <= SMEM_BYTES, "shared memory layout too large");
+
+__device__ __forceinline__ void store_bf16(unsigned char *base, int r, int k, int K, float v) {
+  *reinterpret_cast<__nv_bfloat16 *>(base + canon_offset(r, k, K)) = __float2bfloat16_rn(v);
+}
+
+template <int DTYPE>
+__device__ __forceinline__ float wload(const void *p, int i) {
+  if (DTYPE == 0) return __ldg(static_cast<const float *>(p) + i);
+  return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+
+__device__ __forceinline__ void project9(float o[Q]) {
+  float s = 0.f, sx = 0.f, sy = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    s += o[i];
+    sx += (float)cx(i) * o[i];
+    sy += (float)cy(i) * o[i];
+  }
+  const float k1 = -s * (1.0f / 9.0f), k2 = -sx * (1.0f / 6.0f), k3 = -sy * (1.0f / 6.0f);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) o[i] += k1 + (float)cx(i) * k2 + (float)cy(i) * k3;
+}
+
+struct TileIdx {
+  int b, y, x0;
+};
+
+__device__ __forceinline__ TileIdx tile_index(long long tile, int tiles_x, int ny) {
+  TileIdx t;
+  t.x0 = (int)(tile % tiles_x) * WG_THREADS;
+  t.y = (int)((tile / tiles_x) % ny);
+  t.b = (int)(tile / ((long long)tiles_x * ny));
+  return t;
+}
+
+__device__ __forceinline__ void pull_node(const float *__restrict__ in, size_t plane, int nx,
+                                          int ny, const TileIdx &T, int x, float d[Q]) {
+  const float *gb = in + (size_t)T.b * Q * plane;
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
+    const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
+    d[i] = __ldg(gb + i * plane + (size_t)ys * nx + xs);
+  }
+}
+
+// Read 64 accumulator columns of this thread's row, tanh in bf16x2, write
+// them as K columns 0..63 of the thread's operand row.
+__device__ __forceinline__ void tanh_row_to_operand(uint32_t tm_row, unsigned char *a23, int r) {
+#pragma unroll
+  for (int c = 0; c < HIDDEN; c += 16) {
+    uint32_t v[16];
+    tmem_ld16(tm_row + c, v);
+    tmem_wait_ld();
+    uint32_t p[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      p[q] = tanh_bf16x2(pack_bf16x2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])));
+    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c, K2)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8, K2)) =
+        make_uint4(p[4], p[5], p[6], p[7]);
+  }
+}
+
+template <int DTYPE>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_step_mlp_bf16(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
+                    int batch, CollideParams p, const void *w1, const void *b1, const void *w2,
+                    const void *b2, const void *w3, const void *b3, int *flag, int *timeout_flag) {
+  extern __shared__ unsigned char smem_raw[];
+  Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                      ~uintptr_t(1023));
+  const int tid = threadIdx.x;
+  const int wg = tid / WG_THREADS;  // warpgroup 0 or 1
+  const int r = tid % WG_THREADS;   // row = node within the tile = TMEM lane
+  const int warp_in_wg = r / 32;
+
+  // ---- prologue: weights -> bf16 operand tiles, constant columns, barriers, TMEM
+  for (int e = tid; e < HIDDEN * K1; e += THREADS) {
+    const int n = e / K1, k = e % K1;
+    const float v = k < 9 ? wload<DTYPE>(w1, n * 9 + k) : (k == 9 ? wload<DTYPE>(b1, n) : 0.f);
+    store_bf16(S.w1, n, k, K1, v);
+  }
+  for (int e = tid; e < HIDDEN * K2; e += THREADS) {
+    const int n = e / K2, k = e % K2;
+    const float v =
+        k < HIDDEN ? wload<DTYPE>(w2, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b2, n) : 0.f);
+    store_bf16(S.w2, n, k, K2, v);
+  }
+  for (int e = tid; e < 16 * K2; e += THREADS) {
+    const int n = e / K2, k = e % K2;
+    float v = 0.f;
+    if (n < 9) v = k < HIDDEN ? wload<DTYPE>(w3, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b3, n) : 0.f);
+    store_bf16(S.w3, n, k, K2, v);
+  }
+  // constant K columns 64..79 of this thread's layer-2/3 operand row: 1, 0, ..., 0
+  {
+    unsigned char *a23 = S.a23[wg];
+    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&S.bar[0]), 1);
+    mbar_init(smem_u32(&S.bar[1]), 1);
+    fence_mbarrier_init();
+  }
+  if (tid < 32) {
+    tmem_alloc(smem_u32(&S.taddr), TMEM_COLS);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+
+  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 128);                 // this WG's columns
+  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);   // + lane base
+  const uint32_t bar = smem_u32(&S.bar[wg]);
+  const uint32_t bar_id = 1 + wg;
+  const bool leader = r == 0;
+  unsigned char *a1 = S.a1[wg];
+  unsigned char *a23 = S.a23[wg];
+  const uint64_t da1 = smem_desc(smem_u32(a1), 128, 16 * K1);
+  const uint64_t db1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
+  const uint32_t sa23 = smem_u32(a23), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
+  constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
+
+  const size_t plane = (size_t)nx * ny;
+  const int tiles_x = (nx + WG_THREADS - 1) / WG_THREADS;
+  const long long ntiles = (long long)tiles_x * ny * batch;
+  const long long stride = 2LL * gridDim.x;
+  long long tile = 2LL * blockIdx.x + wg;
+  uint32_t phase = 0;
+  bool fail = false;  // this thread's last bounded wait gave up
+
+  float d[Q];
+  if (tile < ntiles) {
+    const TileIdx T = tile_index(tile, tiles_x, ny);
+    const int x = T.x0 + r;
+    if (x < nx) pull_node(in, plane, nx, ny, T, x, d);
+    else
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = 0.f;
+  }
+
+  for (; tile < ntiles; tile += stride) {
+    const TileIdx T = tile_index(tile, tiles_x, ny);
+    const int x = T.x0 + r;
+    const bool active = x < nx;
+
+    // ---- per-node FP32 pre-processing, layer-1 operand row
+    const Moments m = node_moments(d);
+    if (active) check_stability(m, flag);
+    float deq[Q], xin[Q];
+    shifted_feq(m, deq);
+    const float inv_rho = 1.0f / m.rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+    *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
+        make_uint4(pack_bf16x2(xin[0], xin[1]), pack_bf16x2(xin[2], xin[3]),
+                   pack_bf16x2(xin[4], xin[5]), pack_bf16x2(xin[6], xin[7]));
+    *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
+        make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
+    fence_proxy_async();
+    fence_before_sync();
+    if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    if (leader) {
+      fence_after_sync();
+      mma_bf16(tm_wg + 0, da1, db1, ID64, 0);
+      mma_commit(bar);
+    }
+
+    // ---- prefetch the next tile's populations while the GEMMs run
+    float dn[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dn[i] = 0.f;
+    const long long next = tile + stride;
+    if (next < ntiles) {
+      const TileIdx N = tile_index(next, tiles_x, ny);
+      const int xn = N.x0 + r;
+      if (xn < nx) pull_node(in, plane, nx, ny, N, xn, dn);
+    }
+
+    // ---- layer 1 epilogue: h1 = tanh(D1) -> operand of layer 2
+    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+    if (!fail) {
+      phase ^= 1;
+      fence_after_sync();
+      tanh_row_to_operand(tm_row + 0, a23, r);
+      fence_proxy_async();
+    }
+    fence_before_sync();
+    if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    if (leader) {
+      fence_after_sync();
+#pragma unroll
+      for (int s = 0; s < K2 / 16; ++s)
+        mma_bf16(tm_wg + 64, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+                 smem_desc(sw2 + 256 * s, 128, 16 * K2), ID64, s > 0);
+      mma_commit(bar);
+    }
+
+    // ---- layer 2 epilogue: h2 = tanh(D2) -> operand of layer 3
+    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+    if (!fail) {
+      phase ^= 1;
+      fence_after_sync();
+      tanh_row_to_operand(tm_row + 64, a23, r);
+      fence_proxy_async();
+    }
+    fence_before_sync();
+    if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    if (leader) {
+      fence_after_sync();
+#pragma unroll
+      for (int s = 0; s < K2 / 16; ++s)
+        mma_bf16(tm_wg + 0, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+                 smem_desc(sw3 + 256 * s, 128, 16 * K2), ID16, s > 0);
+      mma_commit(bar);
+    }
+
+    // ---- layer 3 epilogue: projection, BGK + learned correction + force, store
+    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+    if (!fail) {
+      phase ^= 1;
+      fence_after_sync();
+      uint32_t ov[16];
+      tmem_ld16(tm_row + 0, ov);
+      tmem_wait_ld();
+      float o[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
+      project9(o);
+      if (active) {
+        const float rw = m.rho * p.omega;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = fmaf(p.omega, deq[i] - d[i], d[i]) + rw * o[i];
+        if (p.force) add_edm_force_x(m, __ldg(p.force + T.y), d);
+        float *ob = out + (size_t)T.b * Q * plane + (size_t)T.y * nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ob[i * plane] = d[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = dn[i];
+  }
+
+  // uniform verdict of the warpgroup; a thread whose wait gave up drains the
+  // outstanding commit (bounded) before tensor memory is released
+  if (barrier_any(bar_id, WG_THREADS, fail)) {
+    if (leader) atomicOr(timeout_flag, 1);
+    if (fail) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tmem_dealloc(S.taddr, TMEM_COLS);
+}
+
+}  // namespace
+
+cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
+                                 const CollideParams &p, const void *const wp[6], int dtype,
+                                 int *flag, int *timeout_flag, cudaStream_t s) {
+  static int sms = 0;
+  static bool attr_done[2] = {false, false};
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  auto kern = dtype == 0 ? k_step_mlp_bf16<0> : k_step_mlp_bf16<1>;
+  if (!attr_done[dtype]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done[dtype] = true;
+  }
+  const long long tiles = (long long)((g.nx + WG_THREADS - 1) / WG_THREADS) * g.ny * g.batch;
+  long long ctas = (tiles + 1) / 2;
+  if (ctas > 2LL * sms) ctas = 2LL * sms;
+  kern<<<(unsigned)ctas, THREADS, SMEM_BYTES, s>>>(in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1],
+                                                   wp[2], wp[3], wp[4], wp[5], flag, timeout_flag);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm
