@@ -1,0 +1,439 @@
+"""Benchmark of the D2Q9 learned-collision step (the hot path) on GB300.
+
+Workload (one "step"): one fused pull-stream + learned-collision lattice-
+Boltzmann step (MLP 9-64-64-9, tanh, BF16 tensor cores, FP32 populations,
+Kolmogorov forcing by EDM) on a periodic 4096 x 4096 grid, the headline
+configuration.  The state (2 x 604 MB) is larger than L2, so no flush is
+needed between steps.  Also measured in the same run and reported under
+"components": the plain BGK and Smagorinsky-BGK steps and the FP32 learned
+step at 4096^2, and the unrolled training step (32 x 256^2 trajectories,
+16 steps, checkpoint every 4) forward and forward+adjoint.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs one independent replica per rank (launched by torch.distributed.run;
+the path has no data exchange): weak scaling, value = sum over ranks.
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 4096
+TAU = 0.6
+FORCE_AMP, FORCE_MODE = 1e-5, 4
+METRIC = "MLUPS & %HBM/tensor roofline, D2Q9 learned-collision vs BGK at 4096²; fwd+adj ms/step"
+BYTES_PER_NODE = 72  # algorithmic HBM traffic of one FP32 D2Q9 step: 36 B read + 36 B written
+MLP_FLOP_PER_NODE = 2 * (9 * 64 + 64 * 64 + 64 * 9)  # 10,496 algorithmic flops of the MLP
+# Xavier weights with the output layer scaled by 0.3: plain Xavier weights make
+# the learned collision blow up within ~100 steps; 0.3 stays stable for >1500.
+OUT_SCALE = 0.3
+MLP_BF16_SOURCES = ("mlp_bf16.cu", "lattice.cuh", "umma.cuh", "kernels.h")
+WORKLOAD = ("D2Q9 learned-collision LBM step (MLP 9-64-64-9 tanh on tcgen05 BF16, FP32 "
+            "populations), periodic 4096x4096, Kolmogorov forcing F0=1e-5 m=4, tau=0.6, "
+            "random-phase initial field (rms 0.02, seed 2), Xavier weights (seed 3, output "
+            "layer x0.3)")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100", "-f", self.path]
+        if self.gpu_id:
+            cmd[1:1] = ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _init_pg(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def _max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _initial_state(lbm, torch, dev, n=N_GRID, seed=2):
+    from paper_2403_18466_gb300 import inputs
+    rho, ux, uy = inputs.random_velocity_field(n, n, seed=seed, k0=8.0, urms=0.02)
+    lat = lbm.Lattice(n, n, 1, tau=TAU, smag_cs=0.1, force_amp=FORCE_AMP, force_mode=FORCE_MODE,
+                      device=dev)
+    t = lambda a: torch.tensor(a[None], dtype=torch.float32, device=dev)
+    lat.init_equilibrium(t(rho), t(ux), t(uy))
+    return lat
+
+
+def _time_steps(lat, kind, w, steps, torch, stream):
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    lat.step(steps, kind, w)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)  # ms
+
+
+def run_gpu(args):
+    import torch
+    from paper_2403_18466_gb300 import inputs, lbm
+
+    world, rank, local = _dist()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    _init_pg(world, "nccl")
+    lbm.load()
+    hbm_peak, tc_peak, peak_kind = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    nodes = N_GRID * N_GRID
+
+    lat = _initial_state(lbm, torch, dev)
+    theta = torch.tensor(inputs.xavier_mlp(3, out_scale=OUT_SCALE), dtype=torch.float32,
+                         device=dev)
+    w = lbm.weights_struct(theta)
+
+    # ---- headline: BF16 learned-collision steps -------------------------
+    lat.step(max(3, args.warmup), "mlp_bf16", w)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (
+        str(uuid) if uuid is not None else None)
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        ms = _time_steps(lat, "mlp_bf16", w, args.steps, torch, stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    ms_max = _max_over_ranks(ms, world, dev)
+    status = lat.status()
+    ms_step = ms_max / args.steps
+    value = world * nodes / (ms_step * 1e-3) / 1e6  # MLUPS, whole job
+    clocks = clk.summary()
+
+    # ---- roofline of the dominant kernel (the step kernel itself) ---------
+    achieved_gbs = BYTES_PER_NODE * nodes / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
+                "traffic": _traffic_from_profile(MLP_BF16_SOURCES, "k_step_mlp_bf16_2048.md", nodes),
+                "peak_source": peak_kind,
+                "kernel": "k_step_mlp_bf16",
+                "tensor_frac": round(MLP_FLOP_PER_NODE * nodes / (ms / args.steps * 1e-3)
+                                     / (tc_peak * 1e12), 4)}
+
+    # ---- components, same run ------------------------------------------------
+    comps = {}
+    for kind, k in (("bgk", max(args.steps, 200)), ("smag", max(args.steps, 200)),
+                    ("mlp_f32", max(5, args.steps // 50))):
+        lat.step(3, kind, w)
+        t = _time_steps(lat, kind, w, k, torch, stream)
+        g = BYTES_PER_NODE * nodes / (t / k * 1e-3) / 1e9
+        comps[kind] = {"mlups": round(nodes / (t / k * 1e-3) / 1e6, 1),
+                       "ms_per_step": round(t / k, 5), "hbm_gbs": round(g, 1),
+                       "hbm_frac": round(g / hbm_peak, 4)}
+    comps["mlp_bf16"] = {"mlups": round(nodes / (ms_step * 1e-3) / 1e6, 1),
+                         "ms_per_step": round(ms_step, 5), "hbm_gbs": roofline["achieved"],
+                         "hbm_frac": roofline["frac"]}
+    comps["training"] = _time_training(lbm, torch, dev, inputs)
+    del lat
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = _time_e2e(lbm, torch, dev, inputs, w, args.steps, world)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": N_GRID, "ny": N_GRID, "batch": 1,
+                   "mlp_dtype": "bf16 (tcgen05, fp32 accumulate)", "population_dtype": "f32",
+                   "l2": "inputs larger than L2 (state 2 x 604 MB), no flush",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roofline, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": args.steps, "components": comps, "status": lbm.lbm_strerror(status),
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _time_training(lbm, torch, dev, inputs):
+    """Unrolled training step: 32 x 256^2 trajectories, 16 LES steps, checkpoint
+    every 4; forward (FP32 learned collision with checkpoints) and forward +
+    velocity loss + hand-written adjoint."""
+    B, n, L, ck = 32, 256, 16, 4
+    lat = lbm.Lattice(n, n, B, tau=0.500375, force_amp=8e-5, force_mode=4, device=dev)
+    rho = torch.ones((B, n, n), device=dev)
+    ux = torch.tensor(inputs.noise((B, n, n), 5, 0.02), dtype=torch.float32, device=dev)
+    uy = torch.tensor(inputs.noise((B, n, n), 6, 0.02), dtype=torch.float32, device=dev)
+    lat.init_equilibrium(rho, ux, uy)
+    f0 = lat.get_state()
+    theta = torch.tensor(inputs.xavier_mlp(3, out_scale=0.01), dtype=torch.float32, device=dev)
+    w = lbm.weights_struct(theta)
+    ws = torch.empty(lat.record_bytes(L, ck) // 4, dtype=torch.float32, device=dev)
+    dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    res = {}
+    for rep in range(3):
+        lat.set_state(f0)
+        ev[0].record()
+        lat.forward_record(L, ck, w, ws)
+        ev[1].record()
+        loss, g = lat.velocity_loss(ux, uy)
+        lat.backward(g, w, ws, dW, None)
+        ev[2].record()
+        ev[2].synchronize()
+        res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
+    nodes = B * n * n
+    return {"config": "32 x 256^2, 16 steps, checkpoint every 4, FP32 learned collision",
+            "fwd_ms_per_step": round(res["fwd_ms"] / L, 4),
+            "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / L, 4),
+            "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
+            "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
+
+
+def _time_e2e(lbm, torch, dev, inputs, w, steps, world):
+    """The same workload through lbm_run_host: pinned host populations in,
+    `steps` learned-collision steps, density and velocity back to pinned host
+    memory, all inside the timed region (host clock around a synchronous call)."""
+    n = N_GRID
+    rho, ux, uy = inputs.random_velocity_field(n, n, seed=2, k0=8.0, urms=0.02)
+    lat = _initial_state(lbm, torch, dev)
+    f_host = lat.get_state().cpu().pin_memory()
+    outs = [torch.empty((1, n, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+    lat.run_host(f_host, 3, "mlp_bf16", w, *outs)  # warm-up
+    _barrier(world)
+    t0 = time.perf_counter()
+    lat.run_host(f_host, steps, "mlp_bf16", w, *outs)
+    dt = time.perf_counter() - t0
+    dt = _max_over_ranks(dt, world, dev)
+    h2d = f_host.numel() * 4
+    d2h = 3 * n * n * 4
+    return {"value": round(world * n * n * steps / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "note": f"lbm_run_host: {h2d} B in, {steps} steps, {d2h} B out per call"}
+
+
+def cpu_baseline(seconds=12.0, n=1024):
+    """The FP64 oracle (as it stands) on this machine's host cores: learned
+    collision steps on an n x n crop of the same recipe, as many steps as fit
+    in about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_2403_18466_gb300 import inputs
+    rho, ux, uy = inputs.random_velocity_field(n, n, seed=2, k0=8.0 * n / N_GRID, urms=0.02)
+    g = oracle.stream_push(oracle.equilibrium_field(rho[None], ux[None], uy[None]))
+    prm = oracle.params(TAU, force_amp=FORCE_AMP, force_mode=FORCE_MODE)
+    theta = inputs.xavier_mlp(3, out_scale=OUT_SCALE)
+    t0 = time.perf_counter()
+    g = oracle.step(oracle.MLP, g, prm, theta)
+    one = time.perf_counter() - t0
+    k = max(1, min(50, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(oracle.MLP, g, k, prm, theta)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n * n * k / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, learned collision, {n}x{n} crop of the same recipe, "
+                      f"{k} steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2403_18466_gb300 import inputs
+    prm = oracle.params(TAU, force_amp=FORCE_AMP, force_mode=FORCE_MODE)
+    theta = inputs.xavier_mlp(3, out_scale=OUT_SCALE)
+    # each step is one oracle step on an n x n crop of the same recipe; the crop
+    # is the largest of 512, 256, 128, 64 for which all K steps fit ~90 s
+    budget = 90.0
+    for n in (512, 256, 128, 64):
+        rho, ux, uy = inputs.random_velocity_field(n, n, seed=2, k0=max(1.0, 8.0 * n / N_GRID),
+                                                   urms=0.02)
+        g = oracle.stream_push(oracle.equilibrium_field(rho[None], ux[None], uy[None]))
+        t0 = time.perf_counter()
+        g = oracle.step(oracle.MLP, g, prm, theta)  # warm-up and estimate
+        one = time.perf_counter() - t0
+        if one * args.steps <= budget:
+            break
+    for _ in range(max(0, args.warmup - 1)):
+        if one * (args.warmup + args.steps) > 2 * budget:
+            break
+        g = oracle.step(oracle.MLP, g, prm, theta)
+    k = args.steps
+    t0 = time.perf_counter()
+    for _ in range(k):
+        g = oracle.step(oracle.MLP, g, prm, theta)
+    dt = time.perf_counter() - t0
+    value = n * n * k / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"FP64 oracle, learned collision, {n}x{n} crop of the 4096^2 recipe, {k} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+            "n_gpus": world, "steps": k, "warmup": args.warmup, "ms_per_step": round(dt / k * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": N_GRID, "ny": N_GRID, "batch": 1,
+                       "sample": sample},
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """Small case for ncu: `--steps` steps of one collision kind on a
+    `--grid` x `--grid` lattice (no JSON line)."""
+    import torch
+    from paper_2403_18466_gb300 import inputs, lbm
+    dev = torch.device("cuda:0")
+    lbm.load()
+    lat = _initial_state(lbm, torch, dev, n=args.grid)
+    theta = torch.tensor(inputs.xavier_mlp(3, out_scale=OUT_SCALE), dtype=torch.float32,
+                         device=dev)
+    w = lbm.weights_struct(theta)
+    lat.step(args.steps, args.profile, w)
+    torch.cuda.synchronize()
+    rc = lat.status()
+    print(f"profile case {args.profile} {args.grid}^2 x {args.steps}: {lbm.lbm_strerror(rc)}")
+    if rc != lbm.LBM_OK:
+        sys.exit(1)
+
+
+def _traffic_from_profile(kernel_sources, summary, nodes):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    scaled to `nodes`; None if the kernel sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        h = hashlib.sha256()
+        for src in kernel_sources:
+            h.update(open(os.path.join(ROOT, "paper_2403_18466_gb300", "csrc", src), "rb").read())
+        if fields.get("source_sha256") != h.hexdigest():
+            return None
+        return float(fields["dram_bytes_per_launch"]) * nodes / float(fields["nodes_per_launch"])
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", default=None, choices=["bgk", "smag", "mlp_bf16", "mlp_f32"],
+                    help="run a small case of one kernel for ncu and exit")
+    ap.add_argument("--grid", type=int, default=2048)
+    args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,10 +84,20 @@ __device__ __forceinline__ void add_edm_force_x(const Moments &m, float fx, floa
   }
 }
 
-// Flags the run unstable when |u| >= 0.4 or u is not finite.
-__device__ __forceinline__ void check_stability(const Moments &m, int *flag) {
+// True when |u| >= 0.4 or u is not finite.
+__device__ __forceinline__ bool is_unstable(const Moments &m) {
   const float usq = m.ux * m.ux + m.uy * m.uy;
-  if (!(usq < UNSTABLE_USQ)) atomicOr(flag, 1);
+  return !(usq < UNSTABLE_USQ);
+}
+
+// Sets the sticky flag if any calling lane is unstable: one read (and at most
+// one atomic) per warp, so a blown-up state does not serialise on the flag.
+// Call with the same control flow in all lanes that are active.
+__device__ __forceinline__ void flag_unstable(bool bad, int *flag) {
+  const unsigned mask = __ballot_sync(__activemask(), bad);
+  if (mask && (threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+    if (*reinterpret_cast<volatile int *>(flag) == 0) atomicOr(flag, 1);
+  }
 }
 
 __host__ __device__ __forceinline__ int wrap_index(int a, int n) {

@@ -9,15 +9,16 @@
 //
 // Work decomposition.  A tile is 128 consecutive nodes of one row; one
 // warpgroup (128 threads, thread r = node r = tensor-memory lane r) owns a
-// tile at a time, and a CTA holds two warpgroups that walk disjoint tile
-// sequences (persistent, grid = 2 CTAs per SM).  Each layer is one GEMM with
+// tile at a time, and a CTA holds WGS warpgroups; every warpgroup walks its
+// own contiguous range of tiles (persistent, grid = CTAS_PER_SM CTAs per SM).  Each layer is one GEMM with
 // M = 128 nodes:
 //   layer 1: [128 x 16] x [16 x 64]   K = 9 inputs + a constant-1 column (b1) + 6 zeros
 //   layer 2: [128 x 80] x [80 x 64]   K = 64 hidden + constant-1 column (b2) + 15 zeros
 //   layer 3: [128 x 80] x [80 x 16]   N = 9 outputs + 7 zero columns, b3 via the 1-column
 // so the biases ride on the MMA.  Operands live in shared memory in the
-// canonical K-major no-swizzle layout (umma.cuh); the accumulators live in
-// tensor memory (D1: 64 columns, reused by D3; D2: 64 columns).  Between
+// canonical K-major no-swizzle layout (umma.cuh); the accumulators of all
+// three layers share the warpgroup's 64 tensor-memory columns (each layer's
+// accumulator has been read back before the next GEMM is issued).  Between
 // layers each thread reads its own row back with tcgen05.ld, applies tanh on
 // packed bf16 pairs and writes the next operand row.  The populations of the
 // next tile are loaded while the current tile's three GEMMs run.
@@ -39,24 +40,34 @@ namespace {
 using namespace umma;
 
 constexpr int WG_THREADS = 128;
-constexpr int THREADS = 2 * WG_THREADS;
-constexpr int K1 = 16, K2 = 80;  // padded K of layer 1 and of layers 2/3
-constexpr uint32_t TMEM_COLS = 256;  // per CTA: 128 per warpgroup
+#ifndef LBM_BF16_WGS
+#define LBM_BF16_WGS 2
+#endif
+#ifndef LBM_BF16_CTAS_PER_SM
+#define LBM_BF16_CTAS_PER_SM 2
+#endif
+constexpr int WGS = LBM_BF16_WGS;                  // warpgroups per CTA
+constexpr int CTAS_PER_SM = LBM_BF16_CTAS_PER_SM;  // resident CTAs per SM
+constexpr int THREADS = WGS * WG_THREADS;
+constexpr int K1 = 16, K2 = 80;        // padded K of layer 1 and of layers 2/3
+// per CTA: 64 columns per warpgroup, rounded up to a power of two >= 32
+constexpr uint32_t TMEM_COLS = WGS * 64 <= 64 ? 64 : (WGS * 64 <= 128 ? 128 : (WGS * 64 <= 256 ? 256 : 512));
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
 
 struct __align__(1024) Smem {
-  unsigned char w1[HIDDEN * K1 * 2];   // B of layer 1: [64 x 16]
-  unsigned char w2[HIDDEN * K2 * 2];   // B of layer 2: [64 x 80]
-  unsigned char w3[16 * K2 * 2];       // B of layer 3: [16 x 80]
-  unsigned char a1[2][128 * K1 * 2];   // A of layer 1, per warpgroup
-  unsigned char a23[2][128 * K2 * 2];  // A of layers 2 and 3, per warpgroup
-  unsigned long long bar[2];
+  unsigned char w1[HIDDEN * K1 * 2];     // B of layer 1: [64 x 16]
+  unsigned char w2[HIDDEN * K2 * 2];     // B of layer 2: [64 x 80]
+  unsigned char w3[16 * K2 * 2];         // B of layer 3: [16 x 80]
+  unsigned char a1[WGS][128 * K1 * 2];   // A of layer 1, per warpgroup
+  unsigned char a23[WGS][128 * K2 * 2];  // A of layers 2 and 3, per warpgroup
+  unsigned long long bar[WGS];
   uint32_t taddr;
 };
-// Shared memory requested per CTA: padded so that at most two CTAs share an
-// SM (each allocates 256 of the 512 tensor-memory columns).
-constexpr size_t SMEM_BYTES = 84 * 1024;
+// Shared memory requested per CTA: padded so that no more than CTAS_PER_SM
+// CTAs share an SM (their tensor-memory allocations then always fit).
+constexpr size_t SMEM_BYTES = (228 * 1024) / (CTAS_PER_SM + 1) + 1024;
 static_assert(sizeof(Smem) + 1024 <= SMEM_BYTES, "shared memory layout too large");
+static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory oversubscribed");
 
 __device__ __forceinline__ void store_bf16(unsigned char *base, int r, int k, int K, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + canon_offset(r, k, K)) = __float2bfloat16_rn(v);
@@ -81,51 +92,56 @@ __device__ __forceinline__ void project9(float o[Q]) {
   for (int i = 0; i < Q; ++i) o[i] += k1 + (float)cx(i) * k2 + (float)cy(i) * k3;
 }
 
-struct TileIdx {
+// Position of a tile: lattice b, row y, first column x0.  Walked incrementally.
+struct TilePos {
   int b, y, x0;
+  __device__ __forceinline__ void advance(int nx, int ny) {
+    x0 += WG_THREADS;
+    if (x0 >= nx) {
+      x0 = 0;
+      if (++y == ny) {
+        y = 0;
+        ++b;
+      }
+    }
+  }
 };
 
-__device__ __forceinline__ TileIdx tile_index(long long tile, int tiles_x, int ny) {
-  TileIdx t;
-  t.x0 = (int)(tile % tiles_x) * WG_THREADS;
-  t.y = (int)((tile / tiles_x) % ny);
-  t.b = (int)(tile / ((long long)tiles_x * ny));
-  return t;
-}
-
-__device__ __forceinline__ void pull_node(const float *__restrict__ in, size_t plane, int nx,
-                                          int ny, const TileIdx &T, int x, float d[Q]) {
+__device__ __forceinline__ void pull_node(const float *__restrict__ in, int plane, int nx,
+                                          int ny, const TilePos &T, int x, float d[Q]) {
   const float *gb = in + (size_t)T.b * Q * plane;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
+  const int r0 = T.y * nx, rm = ym * nx, rp = yp * nx;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
-    const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
-    d[i] = __ldg(gb + i * plane + (size_t)ys * nx + xs);
+    const int rs = cy(i) == 0 ? r0 : (cy(i) == 1 ? rm : rp);
+    d[i] = __ldg(gb + (size_t)i * plane + rs + xs);
   }
 }
 
-// Read 64 accumulator columns of this thread's row, tanh in bf16x2, write
-// them as K columns 0..63 of the thread's operand row.
+// Read the 64 accumulator columns of this thread's row, tanh on packed bf16
+// pairs, write them as K columns 0..63 of the thread's layer-2/3 operand row.
 __device__ __forceinline__ void tanh_row_to_operand(uint32_t tm_row, unsigned char *a23, int r) {
 #pragma unroll
-  for (int c = 0; c < HIDDEN; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(tm_row + c, v);
+  for (int c = 0; c < HIDDEN; c += 32) {
+    uint32_t v[32];
+    tmem_ld32(tm_row + c, v);
     tmem_wait_ld();
-    uint32_t p[8];
+    uint32_t p[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < 16; ++q)
       p[q] = tanh_bf16x2(pack_bf16x2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])));
-    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c, K2)) = make_uint4(p[0], p[1], p[2], p[3]);
-    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8, K2)) =
-        make_uint4(p[4], p[5], p[6], p[7]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8 * q, K2)) =
+          make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
 }
 
 template <int DTYPE>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     k_step_mlp_bf16(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
                     int batch, CollideParams p, const void *w1, const void *b1, const void *w2,
                     const void *b2, const void *w3, const void *b3, int *flag, int *timeout_flag) {
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(THREADS, 2)
   Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                       ~uintptr_t(1023));
   const int tid = threadIdx.x;
-  const int wg = tid / WG_THREADS;  // warpgroup 0 or 1
+  const int wg = tid / WG_THREADS;  // warpgroup within the CTA
   const int r = tid % WG_THREADS;   // row = node within the tile = TMEM lane
   const int warp_in_wg = r / 32;
 
@@ -152,7 +168,8 @@ __global__ void __launch_bounds__(THREADS, 2)
   for (int e = tid; e < 16 * K2; e += THREADS) {
     const int n = e / K2, k = e % K2;
     float v = 0.f;
-    if (n < 9) v = k < HIDDEN ? wload<DTYPE>(w3, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b3, n) : 0.f);
+    if (n < 9)
+      v = k < HIDDEN ? wload<DTYPE>(w3, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b3, n) : 0.f);
     store_bf16(S.w3, n, k, K2, v);
   }
   // constant K columns 64..79 of this thread's layer-2/3 operand row: 1, 0, ..., 0
@@ -162,8 +179,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
-    mbar_init(smem_u32(&S.bar[0]), 1);
-    mbar_init(smem_u32(&S.bar[1]), 1);
+    for (int k = 0; k < WGS; ++k) mbar_init(smem_u32(&S.bar[k]), 1);
     fence_mbarrier_init();
   }
   if (tid < 32) {
@@ -175,8 +191,8 @@ __global__ void __launch_bounds__(THREADS, 2)
   __syncthreads();
   fence_after_sync();
 
-  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 128);                 // this WG's columns
-  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);   // + lane base
+  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 64);                // this WG's columns
+  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);  // + lane base
   const uint32_t bar = smem_u32(&S.bar[wg]);
   const uint32_t bar_id = 1 + wg;
   const bool leader = r == 0;
@@ -187,35 +203,47 @@ __global__ void __launch_bounds__(THREADS, 2)
   const uint32_t sa23 = smem_u32(a23), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
   constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
 
-  const size_t plane = (size_t)nx * ny;
+  // ---- this warpgroup's contiguous range of tiles
+  const int plane = nx * ny;
   const int tiles_x = (nx + WG_THREADS - 1) / WG_THREADS;
-  const long long ntiles = (long long)tiles_x * ny * batch;
-  const long long stride = 2LL * gridDim.x;
-  long long tile = 2LL * blockIdx.x + wg;
+  const int ntiles = tiles_x * ny * batch;
+  const int nwg = gridDim.x * WGS;
+  const int gwg = blockIdx.x * WGS + wg;
+  const int per = ntiles / nwg, extra = ntiles % nwg;
+  const int t_begin = gwg * per + min(gwg, extra);
+  const int count = per + (gwg < extra ? 1 : 0);
+  TilePos T;
+  T.x0 = (t_begin % tiles_x) * WG_THREADS;
+  T.y = (t_begin / tiles_x) % ny;
+  T.b = t_begin / (tiles_x * ny);
+  const float omega = p.omega;
+
   uint32_t phase = 0;
   bool fail = false;  // this thread's last bounded wait gave up
 
   float d[Q];
-  if (tile < ntiles) {
-    const TileIdx T = tile_index(tile, tiles_x, ny);
-    const int x = T.x0 + r;
-    if (x < nx) pull_node(in, plane, nx, ny, T, x, d);
-    else
 #pragma unroll
-      for (int i = 0; i < Q; ++i) d[i] = 0.f;
-  }
+  for (int i = 0; i < Q; ++i) d[i] = 0.f;
+  if (count > 0 && T.x0 + r < nx) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
 
-  for (; tile < ntiles; tile += stride) {
-    const TileIdx T = tile_index(tile, tiles_x, ny);
+  for (int it = 0; it < count; ++it) {
     const int x = T.x0 + r;
     const bool active = x < nx;
 
     // ---- per-node FP32 pre-processing, layer-1 operand row
-    const Moments m = node_moments(d);
-    if (active) check_stability(m, flag);
-    float deq[Q], xin[Q];
+    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    Moments m;
+    m.drho = drho;
+    m.rho = 1.0f + drho;
+    const float inv_rho = __frcp_rn(m.rho);
+    m.ux = jx * inv_rho;
+    m.uy = jy * inv_rho;
+    flag_unstable(active && is_unstable(m), flag);
+    float deq[Q];
     shifted_feq(m, deq);
-    const float inv_rho = 1.0f / m.rho;
+    float xin[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
     *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
@@ -228,27 +256,24 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     if (leader) {
       fence_after_sync();
-      mma_bf16(tm_wg + 0, da1, db1, ID64, 0);
+      mma_bf16(tm_wg, da1, db1, ID64, 0);
       mma_commit(bar);
     }
 
     // ---- prefetch the next tile's populations while the GEMMs run
+    TilePos N = T;
+    N.advance(nx, ny);
     float dn[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) dn[i] = 0.f;
-    const long long next = tile + stride;
-    if (next < ntiles) {
-      const TileIdx N = tile_index(next, tiles_x, ny);
-      const int xn = N.x0 + r;
-      if (xn < nx) pull_node(in, plane, nx, ny, N, xn, dn);
-    }
+    if (it + 1 < count && N.x0 + r < nx) pull_node(in, plane, nx, ny, N, N.x0 + r, dn);
 
     // ---- layer 1 epilogue: h1 = tanh(D1) -> operand of layer 2
     fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
     if (!fail) {
       phase ^= 1;
       fence_after_sync();
-      tanh_row_to_operand(tm_row + 0, a23, r);
+      tanh_row_to_operand(tm_row, a23, r);
       fence_proxy_async();
     }
     fence_before_sync();
@@ -257,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       fence_after_sync();
 #pragma unroll
       for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg + 64, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
                  smem_desc(sw2 + 256 * s, 128, 16 * K2), ID64, s > 0);
       mma_commit(bar);
     }
@@ -267,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (!fail) {
       phase ^= 1;
       fence_after_sync();
-      tanh_row_to_operand(tm_row + 64, a23, r);
+      tanh_row_to_operand(tm_row, a23, r);
       fence_proxy_async();
     }
     fence_before_sync();
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       fence_after_sync();
 #pragma unroll
       for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg + 0, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
                  smem_desc(sw3 + 256 * s, 128, 16 * K2), ID16, s > 0);
       mma_commit(bar);
     }
@@ -287,24 +312,38 @@ __global__ void __launch_bounds__(THREADS, 2)
       phase ^= 1;
       fence_after_sync();
       uint32_t ov[16];
-      tmem_ld16(tm_row + 0, ov);
+      tmem_ld16(tm_row, ov);
       tmem_wait_ld();
       float o[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
       project9(o);
       if (active) {
-        const float rw = m.rho * p.omega;
+        const float rw = m.rho * omega;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = fmaf(p.omega, deq[i] - d[i], d[i]) + rw * o[i];
-        if (p.force) add_edm_force_x(m, __ldg(p.force + T.y), d);
-        float *ob = out + (size_t)T.b * Q * plane + (size_t)T.y * nx + x;
+        for (int i = 0; i < Q; ++i) d[i] = fmaf(omega, deq[i] - d[i], d[i]) + rw * o[i];
+        if (p.force) {
+          // EDM force (Eq. S5) for F = (fx, 0), cancellation-free form
+          const float fx = __ldg(p.force + T.y);
+          const float sx = 2.0f * m.ux + fx * inv_rho;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) ob[i * plane] = d[i];
+          for (int i = 0; i < Q; ++i) {
+            if (cx(i) == 0) {
+              d[i] -= wf(i) * fx * sx * 1.5f;
+            } else {
+              const float cs = (float)cx(i) * sx + (float)cy(i) * 2.0f * m.uy;
+              d[i] += wf(i) * fx * ((float)cx(i) * (3.0f + 4.5f * cs) - 1.5f * sx);
+            }
+          }
+        }
+        float *ob = out + (size_t)T.b * Q * plane + T.y * nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ob[(size_t)i * plane] = d[i];
       }
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = dn[i];
+    T = N;
   }
 
   // uniform verdict of the warpgroup; a thread whose wait gave up drains the
@@ -339,8 +378,10 @@ cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
     attr_done[dtype] = true;
   }
   const long long tiles = (long long)((g.nx + WG_THREADS - 1) / WG_THREADS) * g.ny * g.batch;
-  long long ctas = (tiles + 1) / 2;
-  if (ctas > 2LL * sms) ctas = 2LL * sms;
+  if ((long long)g.nx * g.ny * g.batch * Q >= (1LL << 31) || tiles >= (1LL << 31))
+    return cudaErrorInvalidValue;  // 32-bit index arithmetic inside the kernel
+  long long ctas = (tiles + WGS - 1) / WGS;
+  if (ctas > (long long)CTAS_PER_SM * sms) ctas = (long long)CTAS_PER_SM * sms;
   kern<<<(unsigned)ctas, THREADS, SMEM_BYTES, s>>>(in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1],
                                                    wp[2], wp[3], wp[4], wp[5], flag, timeout_flag);
   return cudaGetLastError();

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(THREADS)
       d[i] = __ldg(gb + i * plane + (size_t)ys * nx + xs);
     }
     const Moments m = node_moments(d);
-    check_stability(m, flag);
+    flag_unstable(is_unstable(m), flag);
     float deq[Q], xin[Q];
     shifted_feq(m, deq);
     const float inv_rho = 1.0f / m.rho;

@@ -28,11 +28,11 @@ constexpr int SCALAR_THREADS = 128;
 enum { KIND_BGK = 0, KIND_SMAG = 1 };
 
 // Collide one node in place (shifted representation), add the force.
+// Returns true if the node is unstable (|u| >= 0.4 or not finite).
 template <int KIND>
-__device__ __forceinline__ void collide_node(float d[Q], const CollideParams &p, float fx,
-                                             int *flag) {
+__device__ __forceinline__ bool collide_node(float d[Q], const CollideParams &p, float fx) {
   const Moments m = node_moments(d);
-  check_stability(m, flag);
+  const bool bad = is_unstable(m);
   float deq[Q];
   shifted_feq(m, deq);
   float omega = p.omega;
@@ -51,6 +51,7 @@ __device__ __forceinline__ void collide_node(float d[Q], const CollideParams &p,
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] = fmaf(omega, deq[i] - d[i], d[i]);
   if (p.force) add_edm_force_x(m, fx, d);
+  return bad;
 }
 
 __device__ __forceinline__ float4 ldg4(const float *p) {
@@ -107,17 +108,19 @@ __global__ void __launch_bounds__(VEC_THREADS)
   pull_plane4<6>(gb, plane, nx, y, ym, yp, x0, lane, active, v);
   pull_plane4<7>(gb, plane, nx, y, ym, yp, x0, lane, active, v);
   pull_plane4<8>(gb, plane, nx, y, ym, yp, x0, lane, active, v);
-  if (!active) return;
   const float fx = p.force ? __ldg(p.force + y) : 0.0f;
+  bool bad = false;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = v[i][k];
-    collide_node<KIND>(d, p, fx, flag);
+    bad |= collide_node<KIND>(d, p, fx);
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i][k] = d[i];
   }
+  flag_unstable(bad && active, flag);
+  if (!active) return;
 #pragma unroll
   for (int i = 0; i < Q; ++i)
     *reinterpret_cast<float4 *>(ob + i * plane + (size_t)y * nx + x0) =
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(SCALAR_THREADS)
   float *ob = out + (size_t)blockIdx.z * Q * plane;
   float d[Q];
   pull_node(gb, plane, nx, ny, x, y, d);
-  collide_node<KIND>(d, p, p.force ? __ldg(p.force + y) : 0.0f, flag);
+  const bool bad = collide_node<KIND>(d, p, p.force ? __ldg(p.force + y) : 0.0f);
+  flag_unstable(bad, flag);
 #pragma unroll
   for (int i = 0; i < Q; ++i) ob[i * plane + (size_t)y * nx + x] = d[i];
 }
