@@ -169,6 +169,40 @@ int lbm_box_filter(lbm_ctx *ctx_fine, int cg, float *f_coarse);
 int lbm_run_host(lbm_ctx *ctx, const float *f_pre_host, int n, lbm_collision kind,
                  const lbm_weights *w, float *rho_host, float *ux_host, float *uy_host);
 
+/* Velocity loss without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that must not call cudaMalloc -- an
+ * application whose device memory belongs to its own pool allocator (for
+ * example a framework's caching allocator, or a service whose memory budget
+ * is fixed before it starts), or a latency-critical loop where an allocation
+ * or a free would synchronise the device.  Such callers cannot create a
+ * context (lbm_init allocates its scratch), so this function takes the state
+ * buffer directly.
+ *
+ * Computes exactly what lbm_velocity_loss computes, with the same kernels:
+ * `state` is a device state buffer in the library's internal representation
+ * ([b][i][y][x], post-collision populations minus w_i, as returned by
+ * lbm_state_buffer) of a batch x ny x nx lattice; utx, uty [b][y][x]
+ * targets; loss[0] receives L = 1/(2 N B) sum |u - u_t|^2 of the
+ * pre-collision velocity; dL_df (nullable) receives dL/d(pre-collision
+ * populations) [b][i][y][x].  All device pointers, caller-owned; the call is
+ * asynchronous on `cuda_stream` (a cudaStream_t; NULL = legacy default).
+ *
+ * Scratch: the per-block partial sums live in one fixed array of 2^20 floats
+ * (4 MiB) that the library keeps in device memory; every GPU that loads the
+ * library holds it until the process exits.  Sizes needing more partial sums
+ * than that -- ceil(nx / 128) * ny * batch > 1048576 -- are rejected with
+ * LBM_ERR_ARG before anything is launched.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, no allocation) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * array, and each call overwrites the partial sums it uses, so nothing from an
+ * earlier call needs clearing -- but calls that overlap on the GPU (for
+ * example on two streams at once) race on the array and must be serialised by
+ * the caller.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Returns LBM_OK, LBM_ERR_ARG (null pointer, size <= 0, or beyond the limit),
+ * LBM_ERR_UNSUPPORTED (device ordinal >= 256) or LBM_ERR_CUDA. */
+int lbm_velocity_loss_noalloc(const float *state, int nx, int ny, int batch, const float *utx,
+                              const float *uty, float *loss, float *dL_df, void *cuda_stream);
+
 /* Static description of an error code. */
 const char *lbm_strerror(int code);
 

@@ -62,6 +62,7 @@ _SIGS = {
     "lbm_backward": (_i, [_vp, _vp, C.POINTER(lbm_weights), _vp, _sz, _vp, _vp]),
     "lbm_box_filter": (_i, [_vp, _i, _vp]),
     "lbm_run_host": (_i, [_vp, _vp, _i, _i, C.POINTER(lbm_weights), _vp, _vp, _vp]),
+    "lbm_velocity_loss_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "lbm_strerror": (C.c_char_p, [_i]),
 }
 
