@@ -8,7 +8,10 @@
  *   - lattice Boltzmann equation, stream/collide split: Methods, Eq. S2;
  *   - BGK collision: Eq. S3; equilibrium: Eq. S4; EDM forcing: Eq. S5;
  *   - Smagorinsky relaxation time: SI section 1 (Eq. S7 and the strain
- *     from the non-equilibrium stress; closed form derived in the design doc);
+ *     from the non-equilibrium stress, read with the Chapman-Enskog relation
+ *     S = -Pi_neq / (2 rho cs^2 tau_eff), which gives the local closed form
+ *     tau_eff = (tau0 + sqrt(tau0^2 + 18 (C_s Delta)^2 Q / rho)) / 2,
+ *     Q = sqrt(2 Pi_neq : Pi_neq));
  *   - learned collision with mass/momentum projection: Eqs. S10-S12;
  *   - unrolled training and its loss: SI section 2, Eq. S13;
  *   - coarse-graining filter and rescaled tau: SI section 2, Eq. S9.
