@@ -19,15 +19,24 @@
 // canonical K-major no-swizzle layout (umma.cuh); the accumulators of all
 // three layers share the warpgroup's 64 tensor-memory columns (each layer's
 // accumulator has been read back before the next GEMM is issued).  Between
-// layers each thread reads its own row back with tcgen05.ld, applies tanh on
-// packed bf16 pairs and writes the next operand row.  The populations of the
-// next tile are loaded while the current tile's three GEMMs run.
+// layers each thread reads its own row back with tcgen05.ld, rounds pairs to
+// bf16x2 and applies the hardware tanh on the packed pairs, and writes the
+// next operand row.  The populations of the next tile are loaded while the
+// current tile's three GEMMs run.
+//
+// Binding unit: the XU (MUFU) pipe.  Measured on this GPU, per SM sub-
+// partition a warp-wide tanh.approx.bf16x2 occupies the XU pipe for 16 cycles
+// and a cvt to bf16x2 for 4, so the 128 activations of a node cost 10 XU
+// cycles per node per SM; the step cannot exceed ~30 G nodes/s however the
+// GEMMs and memory traffic are scheduled (HBM alone would allow 94 G).
 //
 // Synchronisation per warpgroup: operand rows written by all 128 threads
 // -> fence.proxy.async + named barrier -> one thread issues the MMAs and
-// commits them to the warpgroup's mbarrier -> all threads wait on it (bounded
-// wait; on time-out the kernel sets the timeout flag, drains, frees tensor
-// memory and returns).
+// commits them to the warpgroup's mbarrier -> that thread alone polls the
+// mbarrier (bounded) while the others sleep in a named barrier that also
+// carries its verdict (bar.red.or), so a time-out is seen by the whole
+// warpgroup at once: it leaves the loop, the leader sets the timeout flag and
+// drains its outstanding commit, and tensor memory is freed.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -52,7 +61,16 @@ constexpr int THREADS = WGS * WG_THREADS;
 constexpr int K1 = 16, K2 = 80;        // padded K of layer 1 and of layers 2/3
 // per CTA: 64 columns per warpgroup, rounded up to a power of two >= 32
 constexpr uint32_t TMEM_COLS = WGS * 64 <= 64 ? 64 : (WGS * 64 <= 128 ? 128 : (WGS * 64 <= 256 ? 256 : 512));
+#ifndef LBM_BF16_SLEEP_NS
+#define LBM_BF16_SLEEP_NS 0
+#endif
 constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
+constexpr uint32_t SLEEP_NS = LBM_BF16_SLEEP_NS;  // suspend hint per poll (0: plain polls)
+
+__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase) {
+  if (SLEEP_NS == 0) return mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+  return mbar_wait_sleep_bounded(bar, phase, WAIT_LIMIT / 64, SLEEP_NS);
+}
 
 struct __align__(1024) Smem {
   unsigned char w1[HIDDEN * K1 * 2];     // B of layer 1: [64 x 16]
@@ -65,8 +83,10 @@ struct __align__(1024) Smem {
 };
 // Shared memory requested per CTA: padded so that no more than CTAS_PER_SM
 // CTAs share an SM (their tensor-memory allocations then always fit).
-constexpr size_t SMEM_BYTES = (228 * 1024) / (CTAS_PER_SM + 1) + 1024;
-static_assert(sizeof(Smem) + 1024 <= SMEM_BYTES, "shared memory layout too large");
+constexpr size_t SMEM_NEED = sizeof(Smem) + 1024;
+constexpr size_t SMEM_FLOOR = (228 * 1024) / (CTAS_PER_SM + 1) + 1024;
+constexpr size_t SMEM_BYTES = SMEM_NEED > SMEM_FLOOR ? SMEM_NEED : SMEM_FLOOR;
+static_assert(SMEM_BYTES * CTAS_PER_SM <= 228 * 1024, "shared memory layout too large");
 static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory oversubscribed");
 
 __device__ __forceinline__ void store_bf16(unsigned char *base, int r, int k, int K, float v) {
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
   const float omega = p.omega;
 
   uint32_t phase = 0;
-  bool fail = false;  // this thread's last bounded wait gave up
+  bool fail = false;  // the leader's last bounded wait gave up (leader only)
 
   float d[Q];
 #pragma unroll
@@ -247,13 +267,13 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 #pragma unroll
     for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
     *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
-        make_uint4(pack_bf16x2(xin[0], xin[1]), pack_bf16x2(xin[2], xin[3]),
-                   pack_bf16x2(xin[4], xin[5]), pack_bf16x2(xin[6], xin[7]));
+        make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
+                   pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
     *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
-        make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
+        make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
     fence_proxy_async();
     fence_before_sync();
-    if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
       mma_bf16(tm_wg, da1, db1, ID64, 0);
@@ -269,15 +289,15 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     if (it + 1 < count && N.x0 + r < nx) pull_node(in, plane, nx, ny, N, N.x0 + r, dn);
 
     // ---- layer 1 epilogue: h1 = tanh(D1) -> operand of layer 2
-    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-    if (!fail) {
-      phase ^= 1;
-      fence_after_sync();
-      tanh_row_to_operand(tm_row, a23, r);
-      fence_proxy_async();
-    }
-    fence_before_sync();
+    // (one thread polls the mbarrier; the others sleep in the named barrier)
+    if (leader) fail = !wait_mma(bar, phase);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    phase ^= 1;
+    fence_after_sync();
+    tanh_row_to_operand(tm_row, a23, r);
+    fence_proxy_async();
+    fence_before_sync();
+    named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
@@ -288,15 +308,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     }
 
     // ---- layer 2 epilogue: h2 = tanh(D2) -> operand of layer 3
-    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-    if (!fail) {
-      phase ^= 1;
-      fence_after_sync();
-      tanh_row_to_operand(tm_row, a23, r);
-      fence_proxy_async();
-    }
-    fence_before_sync();
+    if (leader) fail = !wait_mma(bar, phase);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    phase ^= 1;
+    fence_after_sync();
+    tanh_row_to_operand(tm_row, a23, r);
+    fence_proxy_async();
+    fence_before_sync();
+    named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
@@ -307,8 +326,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     }
 
     // ---- layer 3 epilogue: projection, BGK + learned correction + force, store
-    fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-    if (!fail) {
+    if (leader) fail = !wait_mma(bar, phase);
+    if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    {
       phase ^= 1;
       fence_after_sync();
       uint32_t ov[16];
@@ -346,11 +366,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     T = N;
   }
 
-  // uniform verdict of the warpgroup; a thread whose wait gave up drains the
-  // outstanding commit (bounded) before tensor memory is released
-  if (barrier_any(bar_id, WG_THREADS, fail)) {
-    if (leader) atomicOr(timeout_flag, 1);
-    if (fail) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+  // the leader's wait gave up (the whole warpgroup left the loop together):
+  // flag it and drain the outstanding commit (bounded) before tensor memory
+  // is released
+  if (leader && fail) {
+    atomicOr(timeout_flag, 1);
+    wait_mma(bar, phase);
   }
   fence_before_sync();
   __syncthreads();

@@ -136,12 +136,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread may sleep up to hint_ns
+// waiting for the phase instead of spinning on the issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: returns false if the phase did not complete within
 // max_iters polls (each poll may itself suspend for a short while).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   uint32_t max_iters) {
   for (uint32_t it = 0; it < max_iters; ++it)
     if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Bounded wait with sleeping polls: at most max_iters polls of up to hint_ns each.
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint32_t bar, uint32_t parity,
+                                                        uint32_t max_iters, uint32_t hint_ns) {
+  for (uint32_t it = 0; it < max_iters; ++it)
+    if (mbar_try_wait_sleep(bar, parity, hint_ns)) return true;
   return false;
 }
 
@@ -171,6 +191,22 @@ __device__ __forceinline__ bool barrier_any(uint32_t id, uint32_t nthreads, bool
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// Two FP32 values -> bf16x2 with integer ops only (ALU pipe, not the XU pipe
+// that cvt uses): round half away from zero on the magnitude (add half an
+// ulp of bf16 to the bit pattern, keep the high half), lo at the lower address.
+// Valid for finite inputs.
+__device__ __forceinline__ uint32_t pack_bf16x2_alu(float lo, float hi) {
+  const uint32_t a = __float_as_uint(lo) + 0x8000u, b = __float_as_uint(hi) + 0x8000u;
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+// Hardware tanh approximation (FP32).
+__device__ __forceinline__ float tanh_f32(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 // Hardware tanh approximation on packed bf16x2.
