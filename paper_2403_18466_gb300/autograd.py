@@ -1,0 +1,60 @@
+"""Unrolled learned-collision lattice Boltzmann as a ``torch.autograd.Function``.
+
+Forward (SI section 2, "Unrolled training"): load the pre-collision
+populations f0, advance ``nsteps`` steps with the FP32 learned collision while
+recording a checkpoint every ``ckpt_every`` steps (``lbm_forward_record``), and
+return the velocity loss at the final step (``lbm_velocity_loss``).
+Backward: the library's hand-written adjoint (``lbm_backward``) recomputes
+each segment from its checkpoint and returns dL/dtheta (and dL/df0).
+
+Every operation runs in the C ABI's kernels; this module only passes device
+pointers.  The weights are the packed parameter vector of the library
+(w1[64][9], b1, w2[64][64], b2, w3[9][64], b3; LBM_MLP_NPARAMS floats).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import lbm
+
+
+class UnrolledLBM:
+    """Owns the lattice and the checkpoint workspace of one unroll shape."""
+
+    def __init__(self, nx, ny, batch, tau, nsteps, ckpt_every=4, force_amp=0.0, force_mode=0,
+                 device="cuda"):
+        self.lat = lbm.Lattice(nx, ny, batch, tau=tau, force_amp=force_amp,
+                               force_mode=force_mode, device=device)
+        self.nsteps, self.ckpt_every = int(nsteps), int(ckpt_every)
+        nbytes = self.lat.record_bytes(self.nsteps, self.ckpt_every)
+        self.ws = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+        self.dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=device)
+
+    def loss(self, theta, f0, utx, uty):
+        """Differentiable velocity loss of the unroll (w.r.t. theta and f0)."""
+        return _UnrollFn.apply(theta, f0, utx, uty, self)
+
+
+class _UnrollFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, f0, utx, uty, run: UnrolledLBM):
+        theta_c = theta.detach().contiguous()
+        w = lbm.weights_struct(theta_c)
+        lat = run.lat
+        lat.set_state(f0.detach().contiguous())
+        lat.forward_record(run.nsteps, run.ckpt_every, w, run.ws)
+        loss, dL_df = lat.velocity_loss(utx.contiguous(), uty.contiguous(), want_grad=True)
+        ctx.run, ctx.w, ctx.theta = run, w, theta_c
+        ctx.save_for_backward(dL_df)
+        ctx.want_f0 = f0.requires_grad
+        return loss[0].clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (dL_df,) = ctx.saved_tensors
+        run = ctx.run
+        df0 = torch.empty_like(dL_df) if ctx.want_f0 else None
+        run.lat.backward(dL_df, ctx.w, run.ws, run.dW, df0)
+        g_theta = run.dW.clone() * grad_out
+        g_f0 = df0 * grad_out if df0 is not None else None
+        return g_theta, g_f0, None, None, None

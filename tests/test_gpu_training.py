@@ -1,0 +1,135 @@
+"""GPU tests of the training path: the autograd.Function around the hand-written
+adjoint, the DNS -> box-filter data generator, and a short training run.
+
+The gradient of the autograd.Function is checked against torch autograd through
+an independent FP32 restatement of the unrolled learned-collision step written
+here with plain torch ops (test code only; the library never uses it), and
+against central finite differences of the library's own forward.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_18466_gb300 import inputs
+from gpu_helpers import population_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+CX = torch.tensor([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=torch.float32)
+CY = torch.tensor([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=torch.float32)
+W = torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, dtype=torch.float32)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2403_18466_gb300 import lbm as m
+    m.load()
+    return m
+
+
+def _torch_unroll_loss(theta, f0, utx, uty, tau, steps, F0, m):
+    """Plain torch FP32 restatement: pull-stream, moments, feq (Eq. S4), MLP
+    on (f - feq)/rho, projection (Eqs. S11-S12), BGK + (rho/tau) P o (Eq. S10),
+    EDM force (Eq. S5); velocity loss at the end.  f is pre-collision."""
+    dev = f0.device
+    cx, cy, w = CX.to(dev), CY.to(dev), W.to(dev)
+    h = 64
+    W1 = theta[:h * 9].view(h, 9)
+    b1 = theta[h * 9:h * 10]
+    W2 = theta[h * 10:h * 10 + h * h].view(h, h)
+    b2 = theta[h * 10 + h * h:h * 11 + h * h]
+    W3 = theta[h * 11 + h * h:h * 11 + h * h + 9 * h].view(9, h)
+    b3 = theta[h * 11 + h * h + 9 * h:]
+    B, _, ny, nx = f0.shape
+    Fx = (F0 * torch.sin(2 * np.pi * m * torch.arange(ny, device=dev, dtype=torch.float32) / ny)
+          ).view(1, ny, 1)
+
+    def feq(rho, ux, uy):
+        cu = cx.view(1, 9, 1, 1) * ux[:, None] + cy.view(1, 9, 1, 1) * uy[:, None]
+        usq = (ux * ux + uy * uy)[:, None]
+        return w.view(1, 9, 1, 1) * rho[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * usq)
+
+    f = f0
+    for _ in range(steps):
+        rho = f.sum(1)
+        ux = (f * cx.view(1, 9, 1, 1)).sum(1) / rho
+        uy = (f * cy.view(1, 9, 1, 1)).sum(1) / rho
+        fe = feq(rho, ux, uy)
+        x = ((f - fe) / rho[:, None]).permute(0, 2, 3, 1)
+        o = torch.tanh(torch.tanh(x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
+        s, sx, sy = o.sum(-1, keepdim=True), (o * cx).sum(-1, keepdim=True), (o * cy).sum(-1, keepdim=True)
+        oh = (o - s / 9 - cx * sx / 6 - cy * sy / 6).permute(0, 3, 1, 2)
+        post = f + (fe - f) / tau + (rho / tau)[:, None] * oh
+        post = post + feq(rho, ux + Fx / rho, uy) - fe
+        f = torch.stack([torch.roll(post[:, i], shifts=(int(CY[i]), int(CX[i])), dims=(1, 2))
+                         for i in range(9)], 1)
+    rho = f.sum(1)
+    ux = (f * cx.view(1, 9, 1, 1)).sum(1) / rho
+    uy = (f * cy.view(1, 9, 1, 1)).sum(1) / rho
+    return 0.5 * ((ux - utx) ** 2 + (uy - uty) ** 2).mean()
+
+
+def test_autograd_function_matches_torch_autograd_and_fd(lbm):
+    from paper_2403_18466_gb300.autograd import UnrolledLBM
+    B, n, steps, tau, F0, m = 2, 24, 5, 0.6, 1e-4, 1
+    f0 = torch.tensor(population_field(B, n, n, seed=71, neq=0.05), device=DEV)
+    utx = torch.tensor(inputs.noise((B, n, n), 72, 0.03), dtype=torch.float32, device=DEV)
+    uty = torch.tensor(inputs.noise((B, n, n), 73, 0.03), dtype=torch.float32, device=DEV)
+    theta0 = torch.tensor(inputs.xavier_mlp(8, bias_scale=0.3, gain=3.0, out_scale=0.01),
+                          dtype=torch.float32, device=DEV)
+    run = UnrolledLBM(n, n, B, tau, steps, ckpt_every=2, force_amp=F0, force_mode=m, device=DEV)
+    theta = theta0.clone().requires_grad_(True)
+    f0g = f0.clone().requires_grad_(True)
+    loss = run.loss(theta, f0g, utx, uty)
+    loss.backward()
+    # torch autograd through the independent FP32 restatement
+    theta_r = theta0.clone().requires_grad_(True)
+    f0_r = f0.clone().requires_grad_(True)
+    loss_r = _torch_unroll_loss(theta_r, f0_r, utx, uty, tau, steps, F0, m)
+    loss_r.backward()
+    assert abs(loss.item() / loss_r.item() - 1) <= 1e-5
+    scale = theta_r.grad.abs().max().item()
+    assert (theta.grad - theta_r.grad).abs().max().item() <= 1e-4 * scale
+    assert (f0g.grad - f0_r.grad).abs().max().item() <= 1e-4 * f0_r.grad.abs().max().item()
+    # central differences of the library's own forward along a random direction (FP32)
+    d = torch.randn(theta0.shape, generator=torch.Generator().manual_seed(0)).to(DEV)
+    d /= d.norm()
+    eps = 3e-3
+    with torch.no_grad():
+        lp = run.loss(theta0 + eps * d, f0, utx, uty).item()
+        lm = run.loss(theta0 - eps * d, f0, utx, uty).item()
+    fd = (lp - lm) / (2 * eps)
+    dd = float((theta.grad * d).sum())
+    assert abs(fd - dd) <= 2e-2 * abs(dd) + 1e-9
+
+
+def test_data_generation_filter_and_targets(lbm):
+    from paper_2403_18466_gb300 import data
+    ds = data.generate(n=256, cg=8, trajectories=3, unroll=4, spinup=300, stride=64, seed=1)
+    assert ds.f0.shape == (3, 9, 32, 32) and ds.utx.shape == (3, 32, 32)
+    assert torch.isfinite(ds.f0).all() and torch.isfinite(ds.utx).all()
+    assert abs(ds.tau_les - 0.500375) < 1e-12 and abs(ds.force_les - 8e-5) < 1e-15
+    # the coarse states are box averages: mass per lattice equals the fine mass / cg^2
+    rho_c = ds.f0.sum(1).mean().item()
+    assert abs(rho_c - 1.0) < 1e-3
+    # the filter of a GPU state equals the oracle's box filter of the same populations
+    lat = lbm.Lattice(64, 64, 1, device=DEV)
+    f = torch.tensor(population_field(1, 64, 64, seed=3), device=DEV)
+    lat.set_state(f)
+    ref = oracle.box_filter(lat.get_state().double().cpu().numpy(), 8)
+    got = lat.box_filter(8).double().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_short_training_run_reduces_loss(lbm):
+    from paper_2403_18466_gb300 import data, train
+    ds = data.generate(n=256, cg=8, trajectories=4, unroll=4, spinup=300, stride=64, seed=2)
+    theta, hist = train.train(ds, epochs=40, lr=3e-3, out_scale=0.01, verbose=False)
+    assert np.all(np.isfinite(hist))
+    assert min(hist[-5:]) < hist[0]
+    learned, st = train.rollout_loss(ds, "mlp_f32", theta)
+    assert np.isfinite(learned) and st == lbm.LBM_OK
