@@ -248,8 +248,9 @@ def run_gpu(args):
 
 def _time_training(lbm, torch, dev, inputs):
     """Unrolled training step: 32 x 256^2 trajectories, 16 LES steps, checkpoint
-    every 4; forward (FP32 learned collision with checkpoints) and forward +
-    velocity loss + hand-written adjoint."""
+    every 4; forward (learned collision with checkpoints) and forward + velocity
+    loss + hand-written adjoint, for the FP32 pair (CUDA-core MLP and adjoint)
+    and the BF16 pair (tensor-core MLP and tensor-core adjoint)."""
     B, n, L, ck = 32, 256, 16, 4
     lat = lbm.Lattice(n, n, B, tau=0.500375, force_amp=8e-5, force_mode=4, device=dev)
     rho = torch.ones((B, n, n), device=dev)
@@ -262,23 +263,27 @@ def _time_training(lbm, torch, dev, inputs):
     ws = torch.empty(lat.record_bytes(L, ck) // 4, dtype=torch.float32, device=dev)
     dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    res = {}
-    for rep in range(3):
-        lat.set_state(f0)
-        ev[0].record()
-        lat.forward_record(L, ck, w, ws)
-        ev[1].record()
-        loss, g = lat.velocity_loss(ux, uy)
-        lat.backward(g, w, ws, dW, None)
-        ev[2].record()
-        ev[2].synchronize()
-        res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
     nodes = B * n * n
-    return {"config": "32 x 256^2, 16 steps, checkpoint every 4, FP32 learned collision",
-            "fwd_ms_per_step": round(res["fwd_ms"] / L, 4),
-            "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / L, 4),
-            "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
-            "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
+    out = {"config": "32 x 256^2, 16 steps, checkpoint every 4"}
+    for prec in ("f32", "bf16"):
+        res = {}
+        for rep in range(3):
+            lat.set_state(f0)
+            ev[0].record()
+            lat.forward_record(L, ck, w, ws, prec)
+            ev[1].record()
+            loss, g = lat.velocity_loss(ux, uy)
+            lat.backward(g, w, ws, dW, None, prec)
+            ev[2].record()
+            ev[2].synchronize()
+            res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
+        out[prec] = {"fwd_ms_per_step": round(res["fwd_ms"] / L, 4),
+                     "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / L, 4),
+                     "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
+                     "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
+    out["ratio_bf16_fwd_adj_over_f32_fwd"] = round(
+        out["bf16"]["fwd_adj_ms_per_step"] / out["f32"]["fwd_ms_per_step"], 3)
+    return out
 
 
 def _time_e2e(lbm, torch, dev, inputs, w, steps, world):

@@ -157,9 +157,27 @@ int lbm_forward_record(lbm_ctx *ctx, int n, int ckpt_every, const lbm_weights *w
  * w2, b2, w3, b3; overwritten; deterministic) to dW and, if not NULL,
  * dL/d(pre-collision populations at the start) to dL_df0.  Uses the `ws`
  * of the matching lbm_forward_record (n and ckpt_every are remembered by the
- * context); the context's state is not changed. */
+ * context); the context's state is not changed.  The weights must be FP32
+ * (dtype 0). */
 int lbm_backward(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights *w, void *ws,
                  size_t ws_bytes, float *dW, float *dL_df0);
+
+/* The same unrolled training pair with the MLP on the tensor cores:
+ * lbm_forward_record_bf16 advances with LBM_MLP_BF16; lbm_backward_bf16
+ * recomputes segments with LBM_MLP_BF16 and runs the adjoint as tcgen05 GEMMs
+ * (BF16 operands -- activations, adjoints and weights rounded to bf16 --
+ * FP32 accumulation; the per-node chain rule through equilibrium,
+ * projection, BGK and force in FP32), including the weight-gradient sums
+ * over nodes.  Either backward may follow either record: segments are
+ * recomputed with the collision the record used.  Gradients carry the bf16
+ * rounding of activations and adjoints: a few per cent relative L2 of dtheta
+ * for a velocity loss (whose weight-gradient sums over nodes cancel strongly),
+ * against 1e-4 for the FP32 adjoint.  Same arguments and conventions as the
+ * FP32 pair. */
+int lbm_forward_record_bf16(lbm_ctx *ctx, int n, int ckpt_every, const lbm_weights *w, void *ws,
+                            size_t ws_bytes);
+int lbm_backward_bf16(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights *w, void *ws,
+                      size_t ws_bytes, float *dW, float *dL_df0);
 
 /* Coarse-graining filter (SI section 2, with a box average as filter phi):
  * f_coarse[b][i][J][I] = mean over the cg x cg block of the CURRENT

@@ -22,7 +22,11 @@ class UnrolledLBM:
     """Owns the lattice and the checkpoint workspace of one unroll shape."""
 
     def __init__(self, nx, ny, batch, tau, nsteps, ckpt_every=4, force_amp=0.0, force_mode=0,
-                 device="cuda"):
+                 device="cuda", precision="f32"):
+        """precision "f32": FP32 learned collision and FP32 CUDA-core adjoint;
+        "bf16": tensor-core learned collision and tensor-core adjoint."""
+        assert precision in ("f32", "bf16")
+        self.precision = precision
         self.lat = lbm.Lattice(nx, ny, batch, tau=tau, force_amp=force_amp,
                                force_mode=force_mode, device=device)
         self.nsteps, self.ckpt_every = int(nsteps), int(ckpt_every)
@@ -42,7 +46,7 @@ class _UnrollFn(torch.autograd.Function):
         w = lbm.weights_struct(theta_c)
         lat = run.lat
         lat.set_state(f0.detach().contiguous())
-        lat.forward_record(run.nsteps, run.ckpt_every, w, run.ws)
+        lat.forward_record(run.nsteps, run.ckpt_every, w, run.ws, run.precision)
         loss, dL_df = lat.velocity_loss(utx.contiguous(), uty.contiguous(), want_grad=True)
         ctx.run, ctx.w, ctx.theta = run, w, theta_c
         ctx.save_for_backward(dL_df)
@@ -54,7 +58,7 @@ class _UnrollFn(torch.autograd.Function):
         (dL_df,) = ctx.saved_tensors
         run = ctx.run
         df0 = torch.empty_like(dL_df) if ctx.want_f0 else None
-        run.lat.backward(dL_df, ctx.w, run.ws, run.dW, df0)
+        run.lat.backward(dL_df, ctx.w, run.ws, run.dW, df0, run.precision)
         g_theta = run.dW.clone() * grad_out
         g_f0 = df0 * grad_out if df0 is not None else None
         return g_theta, g_f0, None, None, None

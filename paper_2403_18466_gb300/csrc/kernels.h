@@ -71,4 +71,13 @@ cudaError_t launch_adjoint_step(const Grid &g, const float *state_n, const float
                                 float *dw_partials, int rows, int accumulate, cudaStream_t s);
 cudaError_t launch_reduce_dw(const float *dw_partials, int rows, float *dW, cudaStream_t s);
 
+// adjoint_tc.cu ----------------------------------------------------------------
+// Tensor-core adjoint step (BF16 operands, FP32 accumulation); one partial row
+// per warpgroup.
+int adjoint_tc_rows(const Grid &g, int sms);
+cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *lam_next,
+                              float *lam_out, const CollideParams &p, const MlpF32 &w,
+                              float *dw_partials, int rows, int accumulate, int *timeout_flag,
+                              cudaStream_t s);
+
 }  // namespace lbm

@@ -33,6 +33,7 @@ struct lbm_ctx {
   // last lbm_forward_record
   int rec_n, rec_k;
   const void *rec_ws;
+  lbm_collision rec_kind;
 };
 
 namespace {
@@ -91,7 +92,8 @@ cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind
 
 int ensure_dw_partials(lbm_ctx *c) {
   if (c->d_dw_part) return LBM_OK;
-  c->dw_rows = lbm::adjoint_blocks(c->g, c->sms);
+  const int a = lbm::adjoint_blocks(c->g, c->sms), b = lbm::adjoint_tc_rows(c->g, c->sms);
+  c->dw_rows = a > b ? a : b;  // capacity; each adjoint uses its own row count
   CUDA_TRY(cudaMalloc(&c->d_dw_part, (size_t)c->dw_rows * lbm::NPARAMS * sizeof(float)));
   return LBM_OK;
 }
@@ -254,10 +256,12 @@ size_t lbm_record_bytes(const lbm_params *p, int n, int k) {
   return states * state_bytes(p);
 }
 
-int lbm_forward_record(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
-                       size_t ws_bytes) {
+}  // extern "C"
+
+static int forward_record(lbm_ctx *c, lbm_collision kind, int n, int k, const lbm_weights *w,
+                          void *ws, size_t ws_bytes) {
   if (!c || n < 0 || k < 1 || !ws) return LBM_ERR_ARG;
-  if (check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
+  if (!w || check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
   if (ws_bytes < lbm_record_bytes(&c->p, n, k)) return LBM_ERR_ARG;
   const size_t sb = state_bytes(&c->p);
   char *base = static_cast<char *>(ws);
@@ -265,7 +269,7 @@ int lbm_forward_record(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
     if (s % k == 0)
       CUDA_TRY(cudaMemcpyAsync(base + (size_t)(s / k) * sb, c->buf[c->cur], sb,
                                cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], LBM_MLP_F32, w));
+    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w));
     c->cur ^= 1;
   }
   if (n == 0)
@@ -273,18 +277,32 @@ int lbm_forward_record(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
   c->rec_n = n;
   c->rec_k = k;
   c->rec_ws = ws;
+  c->rec_kind = kind;
   return LBM_OK;
 }
 
-int lbm_backward(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w, void *ws,
-                 size_t ws_bytes, float *dW, float *dL_df0) {
+extern "C" int lbm_forward_record(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
+                                  size_t ws_bytes) {
+  return forward_record(c, LBM_MLP_F32, n, k, w, ws, ws_bytes);
+}
+
+extern "C" int lbm_forward_record_bf16(lbm_ctx *c, int n, int k, const lbm_weights *w, void *ws,
+                                       size_t ws_bytes) {
+  return forward_record(c, LBM_MLP_BF16, n, k, w, ws, ws_bytes);
+}
+
+static int backward(lbm_ctx *c, bool tc, const float *dL_df_final, const lbm_weights *w, void *ws,
+                    size_t ws_bytes, float *dW, float *dL_df0) {
   if (!c || !dL_df_final || !ws || !dW) return LBM_ERR_ARG;
-  if (check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
+  if (!w || check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
   if (ws != c->rec_ws) return LBM_ERR_ARG;  // needs the workspace of the last record
+  // segments are recomputed with the collision the record used
+  const lbm_collision kind = c->rec_kind;
   const int n = c->rec_n, k = c->rec_k;
   if (ws_bytes < lbm_record_bytes(&c->p, n, k)) return LBM_ERR_ARG;
   int rc = ensure_dw_partials(c);
   if (rc != LBM_OK) return rc;
+  const int rows = tc ? lbm::adjoint_tc_rows(c->g, c->sms) : lbm::adjoint_blocks(c->g, c->sms);
   const size_t sb = state_bytes(&c->p);
   char *base = static_cast<char *>(ws);
   const int nck = n_checkpoints(n, k);
@@ -303,12 +321,17 @@ int lbm_backward(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w, voi
     // recompute g^{s0+1} .. g^{s0+len-1} into seg[0 .. len-2]
     for (int j = 1; j < len; ++j) {
       const float *in = j == 1 ? ck : seg + (size_t)(j - 2) * sf;
-      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, LBM_MLP_F32, w));
+      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, kind, w));
     }
     for (int j = len - 1; j >= 0; --j) {
       const float *gs = j == 0 ? ck : seg + (size_t)(j - 1) * sf;
-      CUDA_TRY(lbm::launch_adjoint_step(c->g, gs, lam[cur], lam[cur ^ 1], c->cp, wf,
-                                        c->d_dw_part, c->dw_rows, first ? 0 : 1, c->stream));
+      if (tc)
+        CUDA_TRY(lbm::launch_adjoint_tc(c->g, gs, lam[cur], lam[cur ^ 1], c->cp, wf,
+                                        c->d_dw_part, rows, first ? 0 : 1, c->d_flag + 1,
+                                        c->stream));
+      else
+        CUDA_TRY(lbm::launch_adjoint_step(c->g, gs, lam[cur], lam[cur ^ 1], c->cp, wf,
+                                          c->d_dw_part, rows, first ? 0 : 1, c->stream));
       first = false;
       cur ^= 1;
     }
@@ -316,12 +339,24 @@ int lbm_backward(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w, voi
   if (first) {
     CUDA_TRY(cudaMemsetAsync(dW, 0, sizeof(float) * lbm::NPARAMS, c->stream));
   } else {
-    CUDA_TRY(lbm::launch_reduce_dw(c->d_dw_part, c->dw_rows, dW, c->stream));
+    CUDA_TRY(lbm::launch_reduce_dw(c->d_dw_part, rows, dW, c->stream));
   }
   // dL/df_pre(0) = pull(lam^0): g^0 was the push of f_pre(0)
   if (dL_df0) CUDA_TRY(lbm::launch_pull(c->g, lam[cur], dL_df0, c->stream));
   return LBM_OK;
 }
+
+extern "C" int lbm_backward(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w,
+                            void *ws, size_t ws_bytes, float *dW, float *dL_df0) {
+  return backward(c, false, dL_df_final, w, ws, ws_bytes, dW, dL_df0);
+}
+
+extern "C" int lbm_backward_bf16(lbm_ctx *c, const float *dL_df_final, const lbm_weights *w,
+                                 void *ws, size_t ws_bytes, float *dW, float *dL_df0) {
+  return backward(c, true, dL_df_final, w, ws, ws_bytes, dW, dL_df0);
+}
+
+extern "C" {
 
 int lbm_box_filter(lbm_ctx *c, int cg, float *f_coarse) {
   if (!c || !f_coarse || cg < 1) return LBM_ERR_ARG;

@@ -88,6 +88,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr)
       : "memory");
 }
+// Store 16 consecutive columns of this thread's lane (inverse of tmem_ld16).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -208,6 +220,19 @@ __device__ __forceinline__ float tanh_f32(float x) {
   float r;
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+// tanh(a) and its derivative 1 - tanh(a)^2 to a few ulp, from t = e^{-2|a|}:
+// tanh a = sign(a) (1 - t) / (1 + t),  1 - tanh^2 a = 4 t / (1 + t)^2.
+// Two XU operations (ex2, rcp), the same XU cost as one tanh.approx.f32, but
+// the derivative keeps its relative accuracy for saturated units, where
+// 1 - h^2 formed from an approximate h would not.
+__device__ __forceinline__ void tanh_and_derivative(float a, float &h, float &dh) {
+  float t, r;
+  const float e = -2.8853900817779268f * fabsf(a);  // -2 log2(e) |a|
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(e));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
+  h = copysignf((1.0f - t) * r, a);
+  dh = 4.0f * t * r * r;
 }
 // Hardware tanh approximation on packed bf16x2.
 __device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {

@@ -60,6 +60,8 @@ _SIGS = {
     "lbm_record_bytes": (_sz, [C.POINTER(lbm_params), _i, _i]),
     "lbm_forward_record": (_i, [_vp, _i, _i, C.POINTER(lbm_weights), _vp, _sz]),
     "lbm_backward": (_i, [_vp, _vp, C.POINTER(lbm_weights), _vp, _sz, _vp, _vp]),
+    "lbm_forward_record_bf16": (_i, [_vp, _i, _i, C.POINTER(lbm_weights), _vp, _sz]),
+    "lbm_backward_bf16": (_i, [_vp, _vp, C.POINTER(lbm_weights), _vp, _sz, _vp, _vp]),
     "lbm_box_filter": (_i, [_vp, _i, _vp]),
     "lbm_run_host": (_i, [_vp, _vp, _i, _i, C.POINTER(lbm_weights), _vp, _vp, _vp]),
     "lbm_velocity_loss_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -202,15 +204,16 @@ class Lattice:
     def record_bytes(self, n, ckpt_every):
         return lbm_record_bytes(self.params, n, ckpt_every)
 
-    def forward_record(self, n, ckpt_every, weights, ws):
-        _check(self.lib.lbm_forward_record(self.ctx, int(n), int(ckpt_every), C.byref(weights),
-                                           _ptr(ws), ws.numel() * ws.element_size()),
-               "lbm_forward_record")
+    def forward_record(self, n, ckpt_every, weights, ws, precision="f32"):
+        fn = self.lib.lbm_forward_record if precision == "f32" else self.lib.lbm_forward_record_bf16
+        _check(fn(self.ctx, int(n), int(ckpt_every), C.byref(weights), _ptr(ws),
+                  ws.numel() * ws.element_size()), f"lbm_forward_record ({precision})")
 
-    def backward(self, dL_df_final, weights, ws, dW, dL_df0=None):
-        _check(self.lib.lbm_backward(self.ctx, _ptr(dL_df_final), C.byref(weights), _ptr(ws),
-                                     ws.numel() * ws.element_size(), _ptr(dW), _ptr(dL_df0)),
-               "lbm_backward")
+    def backward(self, dL_df_final, weights, ws, dW, dL_df0=None, precision="f32"):
+        fn = self.lib.lbm_backward if precision == "f32" else self.lib.lbm_backward_bf16
+        _check(fn(self.ctx, _ptr(dL_df_final), C.byref(weights), _ptr(ws),
+                  ws.numel() * ws.element_size(), _ptr(dW), _ptr(dL_df0)),
+               f"lbm_backward ({precision})")
 
     def box_filter(self, cg, out=None):
         import torch

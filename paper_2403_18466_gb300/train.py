@@ -2,8 +2,8 @@
 
 Each epoch: evolve every training trajectory for `unroll` coarse steps with the
 learned collision, compute the velocity loss at the final step, backpropagate
-through all steps with the library's hand-written adjoint, and take an Adam
-step (learning rate 1e-4, weight decay 1e-6, Tab. S1).  Plain BGK and
+through all steps with the library's hand-written adjoint (tensor-core pair by
+default, FP32 CUDA-core pair on request), and take an Adam step (learning rate 1e-4, weight decay 1e-6, Tab. S1).  Plain BGK and
 Smagorinsky-BGK LES from the same initial states are evaluated with the same
 loss as the baselines the learned collision is judged against.
 
@@ -35,14 +35,15 @@ def rollout_loss(ds, kind, theta=None, smag_cs=0.1):
 
 
 def train(ds, epochs=200, lr=1e-4, weight_decay=1e-6, ckpt_every=4, seed=3, out_scale=0.01,
-          log_every=10, verbose=True):
+          log_every=10, verbose=True, precision="bf16"):
+    """precision "bf16": tensor-core forward and adjoint; "f32": CUDA-core FP32 pair."""
     dev = ds.f0.device
     B, _, N, _ = ds.f0.shape
     theta = torch.nn.Parameter(torch.tensor(inputs.xavier_mlp(seed, out_scale=out_scale),
                                             dtype=torch.float32, device=dev))
     opt = torch.optim.Adam([theta], lr=lr, weight_decay=weight_decay)
     run = UnrolledLBM(N, N, B, ds.tau_les, ds.unroll, ckpt_every, ds.force_les, ds.force_mode,
-                      device=dev)
+                      device=dev, precision=precision)
     history = []
     t0 = time.perf_counter()
     for ep in range(epochs):
@@ -65,14 +66,15 @@ def main():
     ap.add_argument("--unroll", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--lr", type=float, default=1e-4)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--save", default=None, help="write the trained weights (torch.save)")
     args = ap.parse_args()
     ds = data_mod.generate(n=args.dns, cg=args.cg, trajectories=args.trajectories,
                            unroll=args.unroll)
     base = {k: rollout_loss(ds, k)[0] for k in ("bgk", "smag")}
     print(json.dumps({"baseline_loss": base}), flush=True)
-    theta, hist = train(ds, epochs=args.epochs, lr=args.lr)
-    learned = rollout_loss(ds, "mlp_f32", theta)[0]
+    theta, hist = train(ds, epochs=args.epochs, lr=args.lr, precision=args.precision)
+    learned = rollout_loss(ds, "mlp_bf16" if args.precision == "bf16" else "mlp_f32", theta)[0]
     print(json.dumps({"trained_loss": learned, "first_epoch_loss": hist[0],
                       "baseline_loss": base}), flush=True)
     if args.save:

@@ -128,8 +128,10 @@ def test_data_generation_filter_and_targets(lbm):
 def test_short_training_run_reduces_loss(lbm):
     from paper_2403_18466_gb300 import data, train
     ds = data.generate(n=256, cg=8, trajectories=4, unroll=4, spinup=300, stride=64, seed=2)
-    theta, hist = train.train(ds, epochs=40, lr=3e-3, out_scale=0.01, verbose=False)
-    assert np.all(np.isfinite(hist))
-    assert min(hist[-5:]) < hist[0]
-    learned, st = train.rollout_loss(ds, "mlp_f32", theta)
-    assert np.isfinite(learned) and st == lbm.LBM_OK
+    for prec, kind in (("bf16", "mlp_bf16"), ("f32", "mlp_f32")):
+        theta, hist = train.train(ds, epochs=40, lr=3e-3, out_scale=0.01, verbose=False,
+                                  precision=prec)
+        assert np.all(np.isfinite(hist))
+        assert min(hist[-5:]) < hist[0]
+        learned, st = train.rollout_loss(ds, kind, theta)
+        assert np.isfinite(learned) and st == lbm.LBM_OK
