@@ -184,6 +184,23 @@ int lbm_backward_bf16(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights 
  * pre-collision populations of ctx_fine.  nx, ny must be multiples of cg. */
 int lbm_box_filter(lbm_ctx *ctx_fine, int cg, float *f_coarse);
 
+/* Longitudinal velocity structure functions of the current pre-collision
+ * velocity (SI section 3): S[(p-1)*rmax + r-1] = < [(u(x + r e) - u(x)) . e]^p >
+ * for p = 1..6, r = 1..rmax (1 <= rmax <= 65535), averaged over every node of
+ * every lattice and over the two lattice directions e (periodic).  S is a
+ * device array of 6*rmax doubles; deterministic.  Allocates diagnostics
+ * scratch in the context on first use. */
+int lbm_structure_functions(lbm_ctx *ctx, int rmax, double *S);
+
+/* Shell-averaged kinetic energy spectrum of the current pre-collision
+ * velocity (the energy spectra of the main text): E[k], k = 0..kmax,
+ * E(k) = 1/2 sum over wavevectors with round(|k'|) = k of |u_hat(k')|^2 / N^2
+ * (unnormalised 2D DFT, N = nx*ny, k' in grid units), averaged over the batch,
+ * so that the sum over all shells is <|u|^2>/2.  E is a device array of
+ * kmax+1 doubles; deterministic.  The DFT is a cuFFT call; allocates
+ * diagnostics scratch and an FFT plan in the context on first use. */
+int lbm_energy_spectrum(lbm_ctx *ctx, int kmax, double *E);
+
 /* Host-buffer convenience: copy f_pre_host (pinned or pageable host memory,
  * [b][i][y][x]) in, advance n steps with `kind`, copy the final rho, ux, uy
  * to host arrays (any may be NULL).  Synchronous. */

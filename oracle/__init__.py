@@ -93,6 +93,7 @@ def lib():
             "ora_unroll_grad": (d, [i, i, i, pd, i, pp, pd, pd, pd, pd, pd]),
             "ora_mlp_collide_vjp": (None, [pd, pd, pp, pd, d, d, pd, pd]),
             "ora_feq_field": (None, [i, i, i, pd, pd, pd, pd]),
+            "ora_structure_functions": (None, [i, i, i, pd, pd, i, pd]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -292,3 +293,36 @@ def equilibrium_field(rho, ux, uy):
     out = np.empty((B, 9, ny, nx))
     lib().ora_feq_field(B, ny, nx, _p(rho), _p(ux), _p(uy), _p(out))
     return out
+
+
+def structure_functions(ux, uy, rmax):
+    """Longitudinal S^p(r), p = 1..6, r = 1..rmax, averaged over nodes and the two
+    lattice directions (structure-function definition, SI section 3).
+    Returns an array [6, rmax]; row p-1 is S^p."""
+    ux, uy = _f64(ux), _f64(uy)
+    B, ny, nx = ux.shape
+    out = np.zeros(6 * rmax)
+    lib().ora_structure_functions(B, ny, nx, _p(ux), _p(uy), int(rmax), _p(out))
+    return out.reshape(6, rmax)
+
+
+def energy_spectrum(ux, uy, kmax):
+    """Shell-averaged kinetic energy spectrum of periodic fields [B, ny, nx]:
+    E(k) = 1/2 sum over wavevectors with round(|k|) = k of |u_hat(k)|^2 / N^2,
+    N = nx ny, averaged over the batch (so sum_k E(k) = <|u|^2>/2 when kmax
+    covers every shell).  k in grid units: k_x in [-nx/2, nx/2), same in y.
+    The FFT is numpy's (a library step); the binning is written out here."""
+    ux, uy = _f64(ux), _f64(uy)
+    B, ny, nx = ux.shape
+    N = nx * ny
+    E = np.zeros(kmax + 1)
+    ky = np.fft.fftfreq(ny) * ny
+    kx = np.fft.fftfreq(nx) * nx
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    shell = np.rint(np.sqrt(KX ** 2 + KY ** 2)).astype(int)
+    for b in range(B):
+        e = 0.5 * (np.abs(np.fft.fft2(ux[b])) ** 2 + np.abs(np.fft.fft2(uy[b])) ** 2) / N ** 2
+        for s_, v in zip(shell.ravel(), e.ravel()):
+            if s_ <= kmax:
+                E[s_] += v
+    return E / B

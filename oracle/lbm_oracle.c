@@ -550,3 +550,29 @@ void ora_feq_field(int B, int ny, int nx, const double *rho, const double *ux,
         for (int i = 0; i < 9; ++i) f[idx4(b, i, y, x, ny, nx)] = q[i];
       }
 }
+
+/* Longitudinal velocity structure functions (the paper's structure-function
+ * definition, SI section 3): S^p(r) = < [(u(x + r e) - u(x)) . e]^p > for
+ * p = 1..6 and r = 1..rmax, averaged over every node and over the two lattice
+ * directions e = x^, y^ (periodic).  S is [6][rmax], S[(p-1)*rmax + r-1]. */
+void ora_structure_functions(int B, int ny, int nx, const double *ux, const double *uy,
+                             int rmax, double *S) {
+  for (int k = 0; k < 6 * rmax; ++k) S[k] = 0.0;
+  for (int r = 1; r <= rmax; ++r) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < B; ++b)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const size_t n = ((size_t)b * ny + y) * nx + x;
+          const double dx = ux[((size_t)b * ny + y) * nx + (x + r) % nx] - ux[n];
+          const double dy = uy[((size_t)b * ny + (y + r) % ny) * nx + x] - uy[n];
+          double px = 1.0, py = 1.0;
+          for (int p = 0; p < 6; ++p) {
+            px *= dx;
+            py *= dy;
+            acc[p] += px + py;
+          }
+        }
+    for (int p = 0; p < 6; ++p) S[p * rmax + r - 1] = acc[p] / (2.0 * B * ny * nx);
+  }
+}

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     print(msg, file=sys.stderr)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -80,4 +80,15 @@ cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *
                               float *dw_partials, int rows, int accumulate, int *timeout_flag,
                               cudaStream_t s);
 
+// diag.cu ----------------------------------------------------------------------
+size_t structure_partials_doubles(const Grid &g, int rmax);
+cudaError_t launch_structure_functions(const Grid &g, const float *ux, const float *uy, int rmax,
+                                       double *part, double *S, cudaStream_t s);
+size_t spectrum_rowpart_doubles(const Grid &g, int kmax);
+// u: [2B][ny][nx] (ux of every lattice, then uy), uh: complex [2B][ny][nx/2+1];
+// *plan_io caches the FFT plan (created on first use).
+cudaError_t launch_energy_spectrum(const Grid &g, float *u, void *uh, void **plan_io, int kmax,
+                                   double *rowpart, double *E, cudaStream_t s);
+void destroy_spectrum_plan(void *plan_io);
+
 }  // namespace lbm

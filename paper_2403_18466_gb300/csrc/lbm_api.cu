@@ -30,6 +30,12 @@ struct lbm_ctx {
   float *d_loss_part;   // lbm::loss_partials(g) floats
   float *d_dw_part;     // dw_rows * NPARAMS floats (allocated on first use)
   int dw_rows;
+  // diagnostics scratch (allocated on first use)
+  float *d_diag_u;      // [2B][ny][nx]
+  void *d_diag_uh;      // complex [2B][ny][nx/2+1]
+  double *d_diag_part;  // partial sums
+  size_t diag_part_cap;
+  void *fft_plan;
   // last lbm_forward_record
   int rec_n, rec_k;
   const void *rec_ws;
@@ -95,6 +101,22 @@ int ensure_dw_partials(lbm_ctx *c) {
   const int a = lbm::adjoint_blocks(c->g, c->sms), b = lbm::adjoint_tc_rows(c->g, c->sms);
   c->dw_rows = a > b ? a : b;  // capacity; each adjoint uses its own row count
   CUDA_TRY(cudaMalloc(&c->d_dw_part, (size_t)c->dw_rows * lbm::NPARAMS * sizeof(float)));
+  return LBM_OK;
+}
+
+int ensure_diag(lbm_ctx *c, size_t part_doubles) {
+  if (!c->d_diag_u) {
+    CUDA_TRY(cudaMalloc(&c->d_diag_u, sizeof(float) * 2 * c->g.nodes()));
+    CUDA_TRY(cudaMalloc(&c->d_diag_uh, sizeof(float) * 2 * 2 * (size_t)c->g.batch * c->g.ny *
+                                           (c->g.nx / 2 + 1)));
+  }
+  if (part_doubles > c->diag_part_cap) {
+    cudaFree(c->d_diag_part);
+    c->d_diag_part = nullptr;
+    c->diag_part_cap = 0;
+    CUDA_TRY(cudaMalloc(&c->d_diag_part, sizeof(double) * part_doubles));
+    c->diag_part_cap = part_doubles;
+  }
   return LBM_OK;
 }
 
@@ -181,6 +203,10 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->d_force);
   cudaFree(c->d_loss_part);
   cudaFree(c->d_dw_part);
+  cudaFree(c->d_diag_u);
+  cudaFree(c->d_diag_uh);
+  cudaFree(c->d_diag_part);
+  lbm::destroy_spectrum_plan(c->fft_plan);
   delete c;
 }
 
@@ -357,6 +383,27 @@ extern "C" int lbm_backward_bf16(lbm_ctx *c, const float *dL_df_final, const lbm
 }
 
 extern "C" {
+
+int lbm_structure_functions(lbm_ctx *c, int rmax, double *S) {
+  if (!c || !S || rmax < 1 || rmax > 65535) return LBM_ERR_ARG;
+  const int rc = ensure_diag(c, lbm::structure_partials_doubles(c->g, rmax));
+  if (rc != LBM_OK) return rc;
+  float *ux = c->d_diag_u, *uy = c->d_diag_u + c->g.nodes();
+  CUDA_TRY(lbm::launch_moments(c->g, c->buf[c->cur], nullptr, ux, uy, c->stream));
+  CUDA_TRY(lbm::launch_structure_functions(c->g, ux, uy, rmax, c->d_diag_part, S, c->stream));
+  return LBM_OK;
+}
+
+int lbm_energy_spectrum(lbm_ctx *c, int kmax, double *E) {
+  if (!c || !E || kmax < 0 || kmax > (1 << 24)) return LBM_ERR_ARG;
+  const int rc = ensure_diag(c, lbm::spectrum_rowpart_doubles(c->g, kmax));
+  if (rc != LBM_OK) return rc;
+  float *ux = c->d_diag_u, *uy = c->d_diag_u + c->g.nodes();
+  CUDA_TRY(lbm::launch_moments(c->g, c->buf[c->cur], nullptr, ux, uy, c->stream));
+  CUDA_TRY(lbm::launch_energy_spectrum(c->g, c->d_diag_u, c->d_diag_uh, &c->fft_plan, kmax,
+                                       c->d_diag_part, E, c->stream));
+  return LBM_OK;
+}
 
 int lbm_box_filter(lbm_ctx *c, int cg, float *f_coarse) {
   if (!c || !f_coarse || cg < 1) return LBM_ERR_ARG;

@@ -65,6 +65,8 @@ _SIGS = {
     "lbm_box_filter": (_i, [_vp, _i, _vp]),
     "lbm_run_host": (_i, [_vp, _vp, _i, _i, C.POINTER(lbm_weights), _vp, _vp, _vp]),
     "lbm_velocity_loss_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "lbm_structure_functions": (_i, [_vp, _i, _vp]),
+    "lbm_energy_spectrum": (_i, [_vp, _i, _vp]),
     "lbm_strerror": (C.c_char_p, [_i]),
 }
 
@@ -214,6 +216,21 @@ class Lattice:
         _check(fn(self.ctx, _ptr(dL_df_final), C.byref(weights), _ptr(ws),
                   ws.numel() * ws.element_size(), _ptr(dW), _ptr(dL_df0)),
                f"lbm_backward ({precision})")
+
+    def structure_functions(self, rmax):
+        """[6, rmax] float64 tensor: S^p(r), p = 1..6 (see lbm_structure_functions)."""
+        import torch
+        out = torch.empty(6 * rmax, dtype=torch.float64, device=self.device)
+        _check(self.lib.lbm_structure_functions(self.ctx, int(rmax), _ptr(out)),
+               "lbm_structure_functions")
+        return out.view(6, rmax)
+
+    def energy_spectrum(self, kmax):
+        """[kmax + 1] float64 tensor: E(k) (see lbm_energy_spectrum)."""
+        import torch
+        out = torch.empty(kmax + 1, dtype=torch.float64, device=self.device)
+        _check(self.lib.lbm_energy_spectrum(self.ctx, int(kmax), _ptr(out)), "lbm_energy_spectrum")
+        return out
 
     def box_filter(self, cg, out=None):
         import torch
