@@ -94,6 +94,9 @@ def lib():
             "ora_mlp_collide_vjp": (None, [pd, pd, pp, pd, d, d, pd, pd]),
             "ora_feq_field": (None, [i, i, i, pd, pd, pd, pd]),
             "ora_structure_functions": (None, [i, i, i, pd, pd, i, pd]),
+            "ora_velocity_loss_subset": (d, [i, i, i, pd, pi, i, pd, pd, pd]),
+            "ora_population_loss_subset": (d, [i, i, i, pd, pi, i, pd, pd]),
+            "ora_subsample": (None, [i, i, i, i, pd, pd]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -326,3 +329,39 @@ def energy_spectrum(ux, uy, kmax):
             if s_ <= kmax:
                 E[s_] += v
     return E / B
+
+
+def _idx(idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    return idx, idx.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def velocity_loss_subset(fpre, idx, utx, uty):
+    """Velocity loss on the nodes idx (flat b*ny*nx + y*nx + x) and its gradient
+    (Eq. S13 with the random subset of the unrolled training, velocity form)."""
+    fpre, utx, uty = _f64(fpre), _f64(utx), _f64(uty)
+    idx, pidx = _idx(idx)
+    g = np.empty_like(fpre)
+    L = lib().ora_velocity_loss_subset(*_shape(fpre), _p(fpre), pidx, len(idx), _p(utx), _p(uty),
+                                       _p(g))
+    return L, g
+
+
+def population_loss_subset(g_post, idx, target):
+    """Population loss of Eq. S13 on the nodes idx (sum over the subset and the
+    nine populations, as printed) and its gradient w.r.t. g_post."""
+    g_post, target = _f64(g_post), _f64(target)
+    idx, pidx = _idx(idx)
+    grad = np.empty_like(g_post)
+    L = lib().ora_population_loss_subset(*_shape(g_post), _p(g_post), pidx, len(idx),
+                                         _p(target), _p(grad))
+    return L, grad
+
+
+def subsample(f, cg):
+    """Filter phi of SI section 2: every cg-th node along both axes."""
+    f = _f64(f)
+    B, ny, nx = _shape(f)
+    out = np.empty((B, 9, ny // cg, nx // cg))
+    lib().ora_subsample(B, ny, nx, int(cg), _p(f), _p(out))
+    return out

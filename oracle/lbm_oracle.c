@@ -576,3 +576,63 @@ void ora_structure_functions(int B, int ny, int nx, const double *ux, const doub
     for (int p = 0; p < 6; ++p) S[p * rmax + r - 1] = acc[p] / (2.0 * B * ny * nx);
   }
 }
+
+/* Velocity loss on a subset of nodes (Eq. S13 with the random subset S of the
+ * unrolled training, velocity form): idx are flat node indices b*ny*nx + y*nx + x;
+ * L = 1/(2 |S|) sum_{n in S} |u(n) - u_t(n)|^2, u = j/rho of the given
+ * pre-collision populations; dLdf (nullable, full field) gets the gradient. */
+double ora_velocity_loss_subset(int B, int ny, int nx, const double *fpre, const int *idx,
+                                int count, const double *utx, const double *uty, double *dLdf) {
+  const size_t N = (size_t)ny * nx;
+  if (dLdf)
+    for (size_t k = 0; k < (size_t)B * 9 * N; ++k) dLdf[k] = 0.0;
+  double L = 0.0;
+  for (int s = 0; s < count; ++s) {
+    const size_t n = (size_t)idx[s];
+    const int b = (int)(n / N), y = (int)((n % N) / nx), x = (int)(n % nx);
+    double f[9], rho, ux, uy;
+    for (int i = 0; i < 9; ++i) f[i] = fpre[idx4(b, i, y, x, ny, nx)];
+    node_moments(f, &rho, &ux, &uy);
+    const double dx = ux - utx[n], dy = uy - uty[n];
+    L += dx * dx + dy * dy;
+    if (dLdf)
+      for (int i = 0; i < 9; ++i)
+        dLdf[idx4(b, i, y, x, ny, nx)] +=
+            (dx * (ORA_CX[i] - ux) + dy * (ORA_CY[i] - uy)) / (rho * count);
+  }
+  return L / (2.0 * count);
+}
+
+/* Population loss of Eq. S13 on a subset S of nodes, as the paper writes it (a
+ * plain sum, no normalisation): L = sum_{n in S} sum_i (g_i(n) - t_i(n))^2 for
+ * post-collision populations g (the stored state) and targets t; dLdg
+ * (nullable, full field) gets the gradient 2 (g - t) on S and 0 elsewhere.
+ * A node listed twice counts twice. */
+double ora_population_loss_subset(int B, int ny, int nx, const double *g, const int *idx,
+                                  int count, const double *t, double *dLdg) {
+  const size_t N = (size_t)ny * nx;
+  if (dLdg)
+    for (size_t k = 0; k < (size_t)B * 9 * N; ++k) dLdg[k] = 0.0;
+  double L = 0.0;
+  for (int s = 0; s < count; ++s) {
+    const size_t n = (size_t)idx[s];
+    const int b = (int)(n / N), y = (int)((n % N) / nx), x = (int)(n % nx);
+    for (int i = 0; i < 9; ++i) {
+      const size_t k = idx4(b, i, y, x, ny, nx);
+      const double d = g[k] - t[k];
+      L += d * d;
+      if (dLdg) dLdg[k] += 2.0 * d;
+    }
+  }
+  return L;
+}
+
+/* Coarse-graining by subsampling (SI section 2, filter phi): f_c(I, J) = f(cg I, cg J). */
+void ora_subsample(int B, int ny, int nx, int cg, const double *f, double *fc) {
+  const int NY = ny / cg, NX = nx / cg;
+  for (int b = 0; b < B; ++b)
+    for (int i = 0; i < 9; ++i)
+      for (int J = 0; J < NY; ++J)
+        for (int I = 0; I < NX; ++I)
+          fc[idx4(b, i, J, I, NY, NX)] = f[idx4(b, i, J * cg, I * cg, ny, nx)];
+}

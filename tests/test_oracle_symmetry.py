@@ -8,6 +8,10 @@
   agrees with a numpy reshape-mean, and commutes with free streaming
   (cg fine steps move a population by one coarse cell).
 * Velocity loss: zero at the target, gradient equal to central differences.
+* Subset losses (velocity and population forms of Eq. S13 on a node subset):
+  the all-node velocity subset loss equals the full-field loss, the values
+  equal a numpy gather, gradients vanish off the subset and match central
+  differences on it.  Subsampling filter: a strided numpy slice.
 """
 import numpy as np
 import pytest
@@ -115,3 +119,47 @@ def test_velocity_loss_zero_at_target_and_gradient_by_central_differences():
         fm[idx] -= eps
         fd = (oracle.velocity_loss(fp, utx, uty) - oracle.velocity_loss(fm, utx, uty)) / (2 * eps)
         assert abs(fd - G[idx]) < 1e-7 * np.abs(G).max()
+
+
+def test_subset_losses_definitions_and_gradients():
+    B, ny, nx = 2, 6, 7
+    rho, ux, uy = (np.ones((B, ny, nx)), inputs.noise((B, ny, nx), 14, 0.05),
+                   inputs.noise((B, ny, nx), 15, 0.05))
+    f = oracle.equilibrium_field(rho, ux, uy) + inputs.noise((B, 9, ny, nx), 16, 0.01)
+    utx, uty = inputs.noise((B, ny, nx), 17, 0.05), inputs.noise((B, ny, nx), 18, 0.05)
+    idx = np.array([0, 5, 17, 43, 60, 83])
+    L, G = oracle.velocity_loss_subset(f, idx, utx, uty)
+    # the full-field loss is the subset loss with every node (same normalisation)
+    Lall, _ = oracle.velocity_loss_subset(f, np.arange(B * ny * nx), utx, uty)
+    assert np.isclose(Lall, oracle.velocity_loss(f, utx, uty), rtol=1e-14)
+    _, vx, vy = oracle.moments(f)
+    flat = lambda a: a.reshape(-1)
+    ref = 0.5 * np.mean((flat(vx)[idx] - flat(utx)[idx]) ** 2 + (flat(vy)[idx] - flat(uty)[idx]) ** 2)
+    assert np.isclose(L, ref, rtol=1e-14)
+    # gradient is zero off the subset and matches central differences on it
+    mask = np.zeros(B * ny * nx, bool)
+    mask[idx] = True
+    assert np.all(G.transpose(0, 2, 3, 1).reshape(-1, 9)[~mask] == 0)
+    eps = 1e-6
+    for k in [(0, 3, 0, 0), (0, 7, 0, 5), (1, 2, 1, 5)]:
+        fp, fm = f.copy(), f.copy()
+        fp[k] += eps
+        fm[k] -= eps
+        fd = (oracle.velocity_loss_subset(fp, idx, utx, uty)[0]
+              - oracle.velocity_loss_subset(fm, idx, utx, uty)[0]) / (2 * eps)
+        assert abs(fd - G[k]) <= 1e-7 * np.abs(G).max()
+    t = f + inputs.noise(f.shape, 19, 0.01)
+    Lp, Gp = oracle.population_loss_subset(f, idx, t)
+    d = (f - t).transpose(0, 2, 3, 1).reshape(-1, 9)[idx]
+    assert np.isclose(Lp, np.sum(d ** 2), rtol=1e-14)
+    assert np.allclose(Gp.transpose(0, 2, 3, 1).reshape(-1, 9)[idx], 2 * d, rtol=1e-14)
+    # zero at the target; a repeated node counts twice
+    assert oracle.population_loss_subset(t, idx, t)[0] == 0.0
+    L2, G2 = oracle.population_loss_subset(f, np.array([5, 5]), t)
+    L1, G1 = oracle.population_loss_subset(f, np.array([5]), t)
+    assert np.isclose(L2, 2 * L1, rtol=1e-15) and np.allclose(G2, 2 * G1, rtol=1e-15)
+
+
+def test_subsample_is_strided_slice():
+    f = inputs.noise((2, 9, 12, 16), 20, 1.0)
+    assert np.array_equal(oracle.subsample(f, 4), f[:, :, ::4, ::4])
