@@ -298,6 +298,29 @@ def _time_training(lbm, torch, dev, inputs):
                      "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
     out["ratio_bf16_fwd_adj_over_f32_fwd"] = round(
         out["bf16"]["fwd_adj_ms_per_step"] / out["f32"]["fwd_ms_per_step"], 3)
+    # the paper's training variant: population loss (Eq. S13) on |S| = 512
+    # random nodes after L_T = 12 or 24 unrolled steps, tensor-core pair
+    gen = torch.Generator().manual_seed(11)
+    idx = torch.randperm(nodes, generator=gen)[:512].to(device=dev, dtype=torch.int32)
+    target = lat.stream(f0, -1)
+    for LT in (12, 24):
+        ws = torch.empty(lat.record_bytes(LT, ck) // 4, dtype=torch.float32, device=dev)
+        for rep in range(3):
+            lat.set_state(f0)
+            ev[0].record()
+            lat.forward_record(LT, ck, w, ws, "bf16")
+            ev[1].record()
+            loss, g = lat.population_loss_subset(idx, target)
+            lat.backward(g, w, ws, dW, None, "bf16")
+            ev[2].record()
+            ev[2].synchronize()
+            res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
+        out[f"bf16_subset512_population_LT{LT}"] = {
+            "fwd_adj_ms": round(res["fwd_adj_ms"], 3),
+            "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / LT, 4),
+            "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
+            "workspace_mb": round(ws.numel() * 4 / 2**20, 1)}
+        del ws
     return out
 
 

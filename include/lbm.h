@@ -125,8 +125,9 @@ int lbm_moments(lbm_ctx *ctx, float *rho, float *ux, float *uy);
 float *lbm_state_buffer(lbm_ctx *ctx);
 
 /* Synchronise the stream and return LBM_ERR_UNSTABLE if any step since the
- * last lbm_clear_status flagged a node, a pending CUDA error as
- * LBM_ERR_CUDA, else LBM_OK.  Synchronous. */
+ * last lbm_clear_status flagged a node, LBM_ERR_TIMEOUT if a kernel gave up a
+ * bounded wait, LBM_ERR_ARG if a subset loss met a node index out of range, a
+ * pending CUDA error as LBM_ERR_CUDA, else LBM_OK.  Synchronous. */
 int lbm_status(lbm_ctx *ctx);
 int lbm_clear_status(lbm_ctx *ctx);
 
@@ -137,6 +138,39 @@ int lbm_clear_status(lbm_ctx *ctx);
  * gradient with respect to the pre-collision populations [b][i][y][x]. */
 int lbm_velocity_loss(lbm_ctx *ctx, const float *utx, const float *uty, float *loss,
                       float *dL_df);
+
+/* Losses on a subset S of nodes (SI section 2, "Unrolled training": the loss
+ * is taken on a random subset of lattice points, |S| = 512 in the paper).
+ * idx: device array of `count` node indices n = b*ny*nx + y*nx + x, each in
+ * [0, batch*ny*nx); a repeated index counts once per occurrence.  An index out
+ * of range adds nothing and makes the next lbm_status return LBM_ERR_ARG.
+ * 1 <= count <= batch*ny*nx, else LBM_ERR_ARG before any launch.  loss[0]
+ * (device float) is a deterministic two-pass FP64 reduction.  dL_df
+ * (device, nullable, 9*batch*ny*nx floats) is overwritten with the gradient
+ * with respect to the CURRENT pre-collision populations [b][i][y][x] (zero
+ * off the entries S touches), ready for lbm_backward.
+ *
+ * lbm_velocity_loss_subset: velocity form,
+ *   L = 1/(2|S|) sum_{n in S} |u(n) - u_t(n)|^2, u = j/rho of the pre-collision
+ *   populations, targets utx, uty [b][y][x] (device).
+ * lbm_population_loss_subset: Eq. S13 as printed (a plain sum),
+ *   L = sum_{n in S} sum_i (g_i(n) - t_i(n))^2, g the post-collision
+ *   populations of the last step (the state before streaming) and t the
+ *   target post-collision populations [b][i][y][x] (device), e.g. anti-
+ *   streamed filtered DNS populations (lbm_stream with dir = -1).  The
+ *   gradient of g_i(n) is stored at dL/df_i(n + c_i), where g_i(n) streams to. */
+int lbm_velocity_loss_subset(lbm_ctx *ctx, const int *idx, int count, const float *utx,
+                             const float *uty, float *loss, float *dL_df);
+int lbm_population_loss_subset(lbm_ctx *ctx, const int *idx, int count, const float *target_post,
+                               float *loss, float *dL_df);
+
+/* Streaming of a population field on the context's grid (Eq. S2), out of
+ * place on the context's stream: dir = +1 streams, out_i(x) = in_i(x - c_i);
+ * dir = -1 anti-streams (SI section 2, step 4: post-collision populations at
+ * t from pre-collision ones at t + 1), out_i(x) = in_i(x + c_i).  in, out:
+ * device [b][i][y][x], 9*batch*ny*nx floats, distinct.  The state is not
+ * touched.  LBM_ERR_ARG for a null or identical pointer or another dir. */
+int lbm_stream(lbm_ctx *ctx, int dir, const float *in, float *out);
 
 /* Bytes of the workspace lbm_forward_record / lbm_backward need for an
  * n-step unroll with a checkpoint every ckpt_every steps. */
@@ -183,6 +217,13 @@ int lbm_backward_bf16(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights 
  * f_coarse[b][i][J][I] = mean over the cg x cg block of the CURRENT
  * pre-collision populations of ctx_fine.  nx, ny must be multiples of cg. */
 int lbm_box_filter(lbm_ctx *ctx_fine, int cg, float *f_coarse);
+
+/* Coarse-graining by subsampling, the filter phi the paper uses (SI section
+ * 2: one lattice point in every cg along each axis): f_coarse[b][i][J][I] =
+ * the CURRENT pre-collision populations of ctx_fine at (x, y) = (cg I, cg J).
+ * f_coarse: device, 9*batch*(ny/cg)*(nx/cg) floats.  nx, ny must be
+ * multiples of cg >= 1, else LBM_ERR_ARG. */
+int lbm_subsample(lbm_ctx *ctx_fine, int cg, float *f_coarse);
 
 /* Longitudinal velocity structure functions of the current pre-collision
  * velocity (SI section 3): S[(p-1)*rmax + r-1] = < [(u(x + r e) - u(x)) . e]^p >

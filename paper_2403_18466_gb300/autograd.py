@@ -3,7 +3,10 @@
 Forward (SI section 2, "Unrolled training"): load the pre-collision
 populations f0, advance ``nsteps`` steps with the FP32 learned collision while
 recording a checkpoint every ``ckpt_every`` steps (``lbm_forward_record``), and
-return the velocity loss at the final step (``lbm_velocity_loss``).
+return the loss at the final step: the velocity loss on every node
+(``lbm_velocity_loss``), or a loss on a node subset S, either its velocity form
+(``lbm_velocity_loss_subset``) or the population form of Eq. S13 on the
+post-collision populations of the last step (``lbm_population_loss_subset``).
 Backward: the library's hand-written adjoint (``lbm_backward``) recomputes
 each segment from its checkpoint and returns dL/dtheta (and dL/df0).
 
@@ -36,18 +39,35 @@ class UnrolledLBM:
 
     def loss(self, theta, f0, utx, uty):
         """Differentiable velocity loss of the unroll (w.r.t. theta and f0)."""
-        return _UnrollFn.apply(theta, f0, utx, uty, self)
+        return _UnrollFn.apply(theta, f0, self, ("velocity", None, utx, uty))
+
+    def loss_subset(self, theta, f0, idx, utx=None, uty=None, target_post=None):
+        """Differentiable loss on the nodes idx (int32 device tensor of flat
+        indices b*N*N + y*N + x): the velocity form against (utx, uty), or,
+        with target_post, Eq. S13 against target post-collision populations."""
+        if target_post is not None:
+            return _UnrollFn.apply(theta, f0, self, ("population", idx, target_post, None))
+        return _UnrollFn.apply(theta, f0, self, ("velocity_subset", idx, utx, uty))
+
+
+def _final_loss(lat, spec):
+    form, idx, a, b = spec
+    if form == "velocity":
+        return lat.velocity_loss(a.contiguous(), b.contiguous(), want_grad=True)
+    if form == "velocity_subset":
+        return lat.velocity_loss_subset(idx, a.contiguous(), b.contiguous(), want_grad=True)
+    return lat.population_loss_subset(idx, a.contiguous(), want_grad=True)
 
 
 class _UnrollFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, f0, utx, uty, run: UnrolledLBM):
+    def forward(ctx, theta, f0, run: UnrolledLBM, spec):
         theta_c = theta.detach().contiguous()
         w = lbm.weights_struct(theta_c)
         lat = run.lat
         lat.set_state(f0.detach().contiguous())
         lat.forward_record(run.nsteps, run.ckpt_every, w, run.ws, run.precision)
-        loss, dL_df = lat.velocity_loss(utx.contiguous(), uty.contiguous(), want_grad=True)
+        loss, dL_df = _final_loss(lat, spec)
         ctx.run, ctx.w, ctx.theta = run, w, theta_c
         ctx.save_for_backward(dL_df)
         ctx.want_f0 = f0.requires_grad
@@ -61,4 +81,4 @@ class _UnrollFn(torch.autograd.Function):
         run.lat.backward(dL_df, ctx.w, run.ws, run.dW, df0, run.precision)
         g_theta = run.dW.clone() * grad_out
         g_f0 = df0 * grad_out if df0 is not None else None
-        return g_theta, g_f0, None, None, None
+        return g_theta, g_f0, None, None

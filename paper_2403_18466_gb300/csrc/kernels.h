@@ -46,6 +46,20 @@ int loss_partials(const Grid &g);
 cudaError_t launch_velocity_loss(const Grid &g, const float *state, const float *utx,
                                  const float *uty, float *partials, float *loss, float *dL_df,
                                  cudaStream_t s);
+// Subset losses: per-block FP64 partials into `partials` (>= subset_partials(count)
+// doubles), then a single-block fixed-order sum into loss[0].  dL_df (nullable)
+// is zeroed and receives the gradient w.r.t. the pre-collision populations.
+int subset_partials(int count);
+cudaError_t launch_velocity_loss_subset(const Grid &g, const float *state, const int *idx,
+                                        int count, const float *utx, const float *uty,
+                                        double *partials, float *loss, float *dL_df,
+                                        int *bad_flag, cudaStream_t s);
+cudaError_t launch_population_loss_subset(const Grid &g, const float *state, const int *idx,
+                                          int count, const float *target, double *partials,
+                                          float *loss, float *dL_df, int *bad_flag,
+                                          cudaStream_t s);
+cudaError_t launch_subsample(const Grid &g, const float *state, int cg, float *f_coarse,
+                             cudaStream_t s);
 // push (transpose of the pull) of an adjoint field: out_i(x) = in_i(x + c_i)
 cudaError_t launch_push(const Grid &g, const float *in, float *out, cudaStream_t s);
 // pull of an adjoint field: out_i(x) = in_i(x - c_i)

@@ -25,9 +25,9 @@ struct lbm_ctx {
   int sms;
   CollideParams cp;
   // scratch (library-owned, device)
-  int *d_flag;          // [0] unstable, [1] device wait timeout
+  int *d_flag;          // [0] unstable, [1] device wait timeout, [2] bad node index
   float *d_force;       // ny floats, or nullptr
-  float *d_loss_part;   // lbm::loss_partials(g) floats
+  float *d_loss_part;   // lbm::loss_partials(g) doubles (float or double partials)
   float *d_dw_part;     // dw_rows * NPARAMS floats (allocated on first use)
   int dw_rows;
   // diagnostics scratch (allocated on first use)
@@ -168,8 +168,8 @@ int lbm_init(lbm_ctx **out, const lbm_params *p, float *f_buf0, float *f_buf1,
   c->cp.smag_c18 = (float)(18.0 * (p->smag_cs * p->smag_delta) * (p->smag_cs * p->smag_delta));
   c->cp.force = nullptr;
   int rc = LBM_OK;
-  if (cudaMalloc(&c->d_flag, 2 * sizeof(int)) != cudaSuccess ||
-      cudaMemset(c->d_flag, 0, 2 * sizeof(int)) != cudaSuccess)
+  if (cudaMalloc(&c->d_flag, 3 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_flag, 0, 3 * sizeof(int)) != cudaSuccess)
     rc = LBM_ERR_CUDA;
   if (rc == LBM_OK && p->force_amp != 0.0) {
     // F_x(y) = F0 sin(2 pi m y / ny), evaluated in double on the host
@@ -185,7 +185,7 @@ int lbm_init(lbm_ctx **out, const lbm_params *p, float *f_buf0, float *f_buf1,
     c->cp.force = c->d_force;
   }
   if (rc == LBM_OK &&
-      cudaMalloc(&c->d_loss_part, sizeof(float) * lbm::loss_partials(c->g)) != cudaSuccess)
+      cudaMalloc(&c->d_loss_part, sizeof(double) * lbm::loss_partials(c->g)) != cudaSuccess)
     rc = LBM_ERR_CUDA;
   if (rc != LBM_OK) {
     lbm_destroy(c);
@@ -252,18 +252,19 @@ int lbm_moments(lbm_ctx *c, float *rho, float *ux, float *uy) {
 
 int lbm_status(lbm_ctx *c) {
   if (!c) return LBM_ERR_ARG;
-  int h[2] = {0, 0};
+  int h[3] = {0, 0, 0};
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpy(h, c->d_flag, sizeof(h), cudaMemcpyDeviceToHost));
   if (h[1]) return LBM_ERR_TIMEOUT;
+  if (h[2]) return LBM_ERR_ARG;
   if (h[0]) return LBM_ERR_UNSTABLE;
   return LBM_OK;
 }
 
 int lbm_clear_status(lbm_ctx *c) {
   if (!c) return LBM_ERR_ARG;
-  CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, 2 * sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, 3 * sizeof(int), c->stream));
   return LBM_OK;
 }
 
@@ -272,6 +273,36 @@ int lbm_velocity_loss(lbm_ctx *c, const float *utx, const float *uty, float *los
   if (!c || !utx || !uty || !loss) return LBM_ERR_ARG;
   CUDA_TRY(lbm::launch_velocity_loss(c->g, c->buf[c->cur], utx, uty, c->d_loss_part, loss, dL_df,
                                      c->stream));
+  return LBM_OK;
+}
+
+int lbm_velocity_loss_subset(lbm_ctx *c, const int *idx, int count, const float *utx,
+                             const float *uty, float *loss, float *dL_df) {
+  if (!c || !idx || !utx || !uty || !loss) return LBM_ERR_ARG;
+  if (count < 1 || (size_t)count > c->g.nodes()) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_velocity_loss_subset(c->g, c->buf[c->cur], idx, count, utx, uty,
+                                            reinterpret_cast<double *>(c->d_loss_part), loss,
+                                            dL_df, c->d_flag + 2, c->stream));
+  return LBM_OK;
+}
+
+int lbm_population_loss_subset(lbm_ctx *c, const int *idx, int count, const float *target_post,
+                               float *loss, float *dL_df) {
+  if (!c || !idx || !target_post || !loss) return LBM_ERR_ARG;
+  if (count < 1 || (size_t)count > c->g.nodes()) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_population_loss_subset(c->g, c->buf[c->cur], idx, count, target_post,
+                                              reinterpret_cast<double *>(c->d_loss_part), loss,
+                                              dL_df, c->d_flag + 2, c->stream));
+  return LBM_OK;
+}
+
+int lbm_stream(lbm_ctx *c, int dir, const float *in, float *out) {
+  if (!c || !in || !out || in == out || (dir != 1 && dir != -1)) return LBM_ERR_ARG;
+  // dir +1 streams (out_i(x) = in_i(x - c_i)), the launcher's pull; -1 anti-streams
+  if (dir == 1)
+    CUDA_TRY(lbm::launch_pull(c->g, in, out, c->stream));
+  else
+    CUDA_TRY(lbm::launch_push(c->g, in, out, c->stream));
   return LBM_OK;
 }
 
@@ -409,6 +440,13 @@ int lbm_box_filter(lbm_ctx *c, int cg, float *f_coarse) {
   if (!c || !f_coarse || cg < 1) return LBM_ERR_ARG;
   if (c->g.nx % cg || c->g.ny % cg) return LBM_ERR_ARG;
   CUDA_TRY(lbm::launch_box_filter(c->g, c->buf[c->cur], cg, f_coarse, c->stream));
+  return LBM_OK;
+}
+
+int lbm_subsample(lbm_ctx *c, int cg, float *f_coarse) {
+  if (!c || !f_coarse || cg < 1) return LBM_ERR_ARG;
+  if (c->g.nx % cg || c->g.ny % cg) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_subsample(c->g, c->buf[c->cur], cg, f_coarse, c->stream));
   return LBM_OK;
 }
 

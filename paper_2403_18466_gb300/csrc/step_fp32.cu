@@ -1,7 +1,7 @@
 // step_fp32.cu -- HBM-bound FP32 kernels: the fused pull-stream + BGK /
 // Smagorinsky-BGK step (+ EDM forcing), and the data-movement kernels
-// around it (state in/out, equilibrium init, moments, box filter, velocity
-// loss, adjoint push/pull).
+// around it (state in/out, equilibrium init, moments, box and subsampling
+// filters, full-field and node-subset losses, push/pull of a field).
 //
 // Step kernel (Eq. S2 with the stream/collide split of the Methods section):
 // each node pulls f_i(x) = g_i(x - c_i) from the previous buffer, collides
@@ -316,6 +316,135 @@ __global__ void k_sum_partials(const float *__restrict__ partials, int n, float 
   if (threadIdx.x == 0) loss[0] = (float)(red[0] * (double)scale);
 }
 
+// ---------------------------------------------------------------------------
+// Losses on a node subset S (the training variant of SI section 2): one thread
+// per listed node n = b*ny*nx + y*nx + x.  Per-sample errors in FP64, per-block
+// FP64 partials (fixed order), then k_sum_partials_f64.  The gradient goes to
+// the pre-collision field dL_df (zeroed beforehand by the launcher) with
+// atomicAdd: distinct samples touch distinct entries, and a repeated sample
+// adds the same value again, so the result does not depend on the order.
+// An index outside [0, B ny nx) contributes nothing and sets bad_flag.
+// ---------------------------------------------------------------------------
+constexpr int SUB_THREADS = 256;
+
+__device__ __forceinline__ bool decode_node(int n, int nx, int ny, int batch, int &x, int &y,
+                                            int &b) {
+  const long long plane = (long long)nx * ny;
+  if (n < 0 || (long long)n >= plane * batch) return false;
+  b = (int)(n / plane);
+  const int r = (int)(n - (long long)b * plane);
+  y = r / nx;
+  x = r - y * nx;
+  return true;
+}
+
+__device__ __forceinline__ void block_sum_f64(double e, double *__restrict__ partials) {
+  __shared__ double red[SUB_THREADS];
+  red[threadIdx.x] = e;
+  __syncthreads();
+  for (int w = SUB_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// e = |u(n) - u_t(n)|^2 of the pre-collision populations at n;
+// dL/df_i(n) = inv_count ((u - u_t).(c_i - u)) / rho   (L = sum e / (2 |S|)).
+__global__ void __launch_bounds__(SUB_THREADS)
+    k_velocity_loss_subset(const float *__restrict__ st, const int *__restrict__ idx, int count,
+                           const float *__restrict__ utx, const float *__restrict__ uty,
+                           double *__restrict__ partials, float *__restrict__ dL_df, int nx,
+                           int ny, int batch, float inv_count, int *bad_flag) {
+  const int s = blockIdx.x * SUB_THREADS + threadIdx.x;
+  double e = 0.0;
+  if (s < count) {
+    int x, y, b;
+    if (!decode_node(idx[s], nx, ny, batch, x, y, b)) {
+      atomicOr(bad_flag, 1);
+    } else {
+      const size_t plane = (size_t)nx * ny;
+      float d[Q];
+      pull_node(st + (size_t)b * Q * plane, plane, nx, ny, x, y, d);
+      const Moments m = node_moments(d);
+      const size_t n = (size_t)b * plane + (size_t)y * nx + x;
+      const float dx = m.ux - utx[n], dy = m.uy - uty[n];
+      e = (double)dx * dx + (double)dy * dy;
+      if (dL_df) {
+        const float inv = inv_count / m.rho;
+        float *o = dL_df + (size_t)b * Q * plane + (size_t)y * nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          atomicAdd(o + i * plane, inv * (dx * ((float)cx(i) - m.ux) + dy * ((float)cy(i) - m.uy)));
+      }
+    }
+  }
+  block_sum_f64(e, partials);
+}
+
+// e = sum_i (g_i(n) - t_i(n))^2 with g the stored post-collision populations
+// (g_i = state_i + w_i, formed in FP64) and t the target [b][i][y][x];
+// dL/dg_i(n) = 2 (g_i - t_i) lands on the pre-collision entry it streams to,
+// dL/df_i(n + c_i) (since f_i(x) = g_i(x - c_i)).
+__global__ void __launch_bounds__(SUB_THREADS)
+    k_population_loss_subset(const float *__restrict__ st, const int *__restrict__ idx, int count,
+                             const float *__restrict__ target, double *__restrict__ partials,
+                             float *__restrict__ dL_df, int nx, int ny, int batch,
+                             int *bad_flag) {
+  const int s = blockIdx.x * SUB_THREADS + threadIdx.x;
+  double e = 0.0;
+  if (s < count) {
+    int x, y, b;
+    if (!decode_node(idx[s], nx, ny, batch, x, y, b)) {
+      atomicOr(bad_flag, 1);
+    } else {
+      const size_t plane = (size_t)nx * ny, base = (size_t)b * Q * plane;
+      const size_t at = (size_t)y * nx + x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double d = ((double)st[base + i * plane + at] + (double)wf(i)) -
+                         (double)target[base + i * plane + at];
+        e += d * d;
+        if (dL_df) {
+          const int xs = wrap_index(x + cx(i), nx), ys = wrap_index(y + cy(i), ny);
+          atomicAdd(dL_df + base + i * plane + (size_t)ys * nx + xs, (float)(2.0 * d));
+        }
+      }
+    }
+  }
+  block_sum_f64(e, partials);
+}
+
+// Single block: loss = scale * sum(partials), fixed order (strided then tree).
+__global__ void k_sum_partials_f64(const double *__restrict__ partials, int n, double scale,
+                                   float *loss) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) a += partials[i];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[0] = (float)(red[0] * scale);
+}
+
+// Subsampling filter phi (SI section 2): the coarse node (I, J) takes the fine
+// pre-collision populations at (cg I, cg J), f_i = state_i(x - c_i) + w_i.
+__global__ void k_subsample(const float *__restrict__ st, float *__restrict__ fc, int nx, int ny,
+                            int cg) {
+  const int NX = nx / cg, NY = ny / cg;
+  const int I = blockIdx.x * NT + threadIdx.x, J = blockIdx.y, b = blockIdx.z;
+  if (I >= NX) return;
+  const size_t plane = (size_t)nx * ny, cplane = (size_t)NX * NY;
+  float d[Q];
+  pull_node(st + (size_t)b * Q * plane, plane, nx, ny, I * cg, J * cg, d);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    fc[(size_t)b * Q * cplane + i * cplane + (size_t)J * NX + I] = d[i] + wf(i);
+}
+
 // out_i(x) = in_i(x + DIR c_i), DIR = +1 push (transpose of the pull), -1 pull.
 template <int DIR>
 __global__ void k_shift(const float *__restrict__ in, float *__restrict__ out, int nx, int ny) {
@@ -381,6 +510,50 @@ cudaError_t launch_velocity_loss(const Grid &g, const float *state, const float 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<1, 256, 0, s>>>(partials, loss_partials(g), 0.5f * inv_nb, loss);
+  return cudaGetLastError();
+}
+
+int subset_partials(int count) { return (count + SUB_THREADS - 1) / SUB_THREADS; }
+
+cudaError_t launch_velocity_loss_subset(const Grid &g, const float *state, const int *idx,
+                                        int count, const float *utx, const float *uty,
+                                        double *partials, float *loss, float *dL_df,
+                                        int *bad_flag, cudaStream_t s) {
+  if (dL_df) {
+    cudaError_t e = cudaMemsetAsync(dL_df, 0, g.state_floats() * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = subset_partials(count);
+  k_velocity_loss_subset<<<blocks, SUB_THREADS, 0, s>>>(state, idx, count, utx, uty, partials,
+                                                        dL_df, g.nx, g.ny, g.batch,
+                                                        (float)(1.0 / count), bad_flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials_f64<<<1, 256, 0, s>>>(partials, blocks, 0.5 / count, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_population_loss_subset(const Grid &g, const float *state, const int *idx,
+                                          int count, const float *target, double *partials,
+                                          float *loss, float *dL_df, int *bad_flag,
+                                          cudaStream_t s) {
+  if (dL_df) {
+    cudaError_t e = cudaMemsetAsync(dL_df, 0, g.state_floats() * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = subset_partials(count);
+  k_population_loss_subset<<<blocks, SUB_THREADS, 0, s>>>(state, idx, count, target, partials,
+                                                          dL_df, g.nx, g.ny, g.batch, bad_flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials_f64<<<1, 256, 0, s>>>(partials, blocks, 1.0, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subsample(const Grid &g, const float *state, int cg, float *f_coarse,
+                             cudaStream_t s) {
+  dim3 grid((g.nx / cg + NT - 1) / NT, g.ny / cg, g.batch);
+  k_subsample<<<grid, NT, 0, s>>>(state, f_coarse, g.nx, g.ny, cg);
   return cudaGetLastError();
 }
 

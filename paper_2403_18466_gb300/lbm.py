@@ -63,6 +63,10 @@ _SIGS = {
     "lbm_forward_record_bf16": (_i, [_vp, _i, _i, C.POINTER(lbm_weights), _vp, _sz]),
     "lbm_backward_bf16": (_i, [_vp, _vp, C.POINTER(lbm_weights), _vp, _sz, _vp, _vp]),
     "lbm_box_filter": (_i, [_vp, _i, _vp]),
+    "lbm_subsample": (_i, [_vp, _i, _vp]),
+    "lbm_velocity_loss_subset": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "lbm_population_loss_subset": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "lbm_stream": (_i, [_vp, _i, _vp, _vp]),
     "lbm_run_host": (_i, [_vp, _vp, _i, _i, C.POINTER(lbm_weights), _vp, _vp, _vp]),
     "lbm_velocity_loss_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "lbm_structure_functions": (_i, [_vp, _i, _vp]),
@@ -140,10 +144,10 @@ class Lattice:
         self.device = torch.device(device)
         self.bufs = [torch.zeros(self.shape, dtype=torch.float32, device=self.device)
                      for _ in range(2)]
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.cuda_stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         ctx = C.c_void_p()
         _check(self.lib.lbm_init(C.byref(ctx), C.byref(self.params), _ptr(self.bufs[0]),
-                                 _ptr(self.bufs[1]), C.c_void_p(self.stream.cuda_stream)),
+                                 _ptr(self.bufs[1]), C.c_void_p(self.cuda_stream.cuda_stream)),
                "lbm_init")
         self.ctx = ctx
 
@@ -174,6 +178,15 @@ class Lattice:
     def state_buffer(self):
         return self.lib.lbm_state_buffer(self.ctx)
 
+    def state_tensor(self):
+        """The torch buffer holding the current internal state (post-collision
+        populations minus the lattice weights, [b][i][y][x]); a view, not a copy."""
+        p = self.state_buffer()
+        for b in self.bufs:
+            if b.data_ptr() == p:
+                return b
+        raise LbmError("state buffer is not one of this lattice's tensors")
+
     # -- stepping -----------------------------------------------------------
     def step(self, n, kind="bgk", weights=None):
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
@@ -202,6 +215,33 @@ class Lattice:
         _check(self.lib.lbm_velocity_loss(self.ctx, _ptr(utx), _ptr(uty), _ptr(loss), _ptr(g)),
                "lbm_velocity_loss")
         return loss, g
+
+    def velocity_loss_subset(self, idx, utx, uty, want_grad=True):
+        """Velocity loss on the nodes idx (int32 device tensor of flat indices)."""
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        g = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_grad else None
+        _check(self.lib.lbm_velocity_loss_subset(self.ctx, _ptr(idx), int(idx.numel()), _ptr(utx),
+                                                 _ptr(uty), _ptr(loss), _ptr(g)),
+               "lbm_velocity_loss_subset")
+        return loss, g
+
+    def population_loss_subset(self, idx, target_post, want_grad=True):
+        """Eq. S13 on the nodes idx against target post-collision populations."""
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        g = torch.empty(self.shape, dtype=torch.float32, device=self.device) if want_grad else None
+        _check(self.lib.lbm_population_loss_subset(self.ctx, _ptr(idx), int(idx.numel()),
+                                                   _ptr(target_post), _ptr(loss), _ptr(g)),
+               "lbm_population_loss_subset")
+        return loss, g
+
+    def stream(self, f, direction=1, out=None):
+        """Stream (+1) or anti-stream (-1) a population field on this grid."""
+        import torch
+        out = torch.empty_like(f) if out is None else out
+        _check(self.lib.lbm_stream(self.ctx, int(direction), _ptr(f), _ptr(out)), "lbm_stream")
+        return out
 
     def record_bytes(self, n, ckpt_every):
         return lbm_record_bytes(self.params, n, ckpt_every)
@@ -238,6 +278,15 @@ class Lattice:
         out = torch.empty((B, 9, ny // cg, nx // cg), dtype=torch.float32,
                           device=self.device) if out is None else out
         _check(self.lib.lbm_box_filter(self.ctx, int(cg), _ptr(out)), "lbm_box_filter")
+        return out
+
+    def subsample(self, cg, out=None):
+        """Filter phi: the pre-collision populations at every cg-th node."""
+        import torch
+        B, _, ny, nx = self.shape
+        out = torch.empty((B, 9, ny // cg, nx // cg), dtype=torch.float32,
+                          device=self.device) if out is None else out
+        _check(self.lib.lbm_subsample(self.ctx, int(cg), _ptr(out)), "lbm_subsample")
         return out
 
     def run_host(self, f_pre_host, n, kind="bgk", weights=None, rho=None, ux=None, uy=None):

@@ -86,3 +86,19 @@ def test_smagorinsky_les_spectrum_at_128_matches_oracle(lbm):
     big = R > 1e-6 * R.max()
     assert np.allclose(E[big], R[big], rtol=1e-3)
     assert lat.status() == lbm.LBM_OK
+
+
+def test_les_run_records_statistics(lbm):
+    """The long-run driver: spectra and structure functions every `every`
+    steps, finite, S^2 positive and rising at small r, and the ESS slope of S^3
+    against itself equal to one."""
+    from paper_2403_18466_gb300 import les
+    res = les.run(n=64, kind="smag", steps=300, every=100, rmax=12, kmax=46)
+    assert res["steps"] == [100, 200, 300]
+    assert res["E"].shape == (3, 47) and res["S"].shape == (3, 6, 12)
+    assert np.all(np.isfinite(res["E"])) and np.all(np.isfinite(res["S"]))
+    assert res["status"] == lbm.lbm_strerror(lbm.LBM_OK)
+    # S^2 > 0 and grows with r at small separations in a smooth field
+    assert np.all(res["S"][:, 1, :] > 0) and np.all(np.diff(res["S"][-1, 1, :4]) > 0)
+    xi = les.ess_exponents(res["S"].mean(0))
+    assert abs(xi[2] - 1.0) < 1e-12 and np.all(np.isfinite(xi))

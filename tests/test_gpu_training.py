@@ -31,10 +31,11 @@ def lbm():
     return m
 
 
-def _torch_unroll_loss(theta, f0, utx, uty, tau, steps, F0, m):
+def _torch_unroll(theta, f0, tau, steps, F0, m):
     """Plain torch FP32 restatement: pull-stream, moments, feq (Eq. S4), MLP
     on (f - feq)/rho, projection (Eqs. S11-S12), BGK + (rho/tau) P o (Eq. S10),
-    EDM force (Eq. S5); velocity loss at the end.  f is pre-collision."""
+    EDM force (Eq. S5).  f0 is pre-collision; returns the post-collision
+    populations of the last step and the pre-collision populations after it."""
     dev = f0.device
     cx, cy, w = CX.to(dev), CY.to(dev), W.to(dev)
     h = 64
@@ -53,7 +54,7 @@ def _torch_unroll_loss(theta, f0, utx, uty, tau, steps, F0, m):
         usq = (ux * ux + uy * uy)[:, None]
         return w.view(1, 9, 1, 1) * rho[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * usq)
 
-    f = f0
+    f, post = f0, None
     for _ in range(steps):
         rho = f.sum(1)
         ux = (f * cx.view(1, 9, 1, 1)).sum(1) / rho
@@ -67,10 +68,24 @@ def _torch_unroll_loss(theta, f0, utx, uty, tau, steps, F0, m):
         post = post + feq(rho, ux + Fx / rho, uy) - fe
         f = torch.stack([torch.roll(post[:, i], shifts=(int(CY[i]), int(CX[i])), dims=(1, 2))
                          for i in range(9)], 1)
+    return post, f
+
+
+def _torch_unroll_loss(theta, f0, utx, uty, tau, steps, F0, m):
+    """Velocity loss at the end of the restated unroll."""
+    _, f = _torch_unroll(theta, f0, tau, steps, F0, m)
+    cx, cy = CX.to(f0.device), CY.to(f0.device)
     rho = f.sum(1)
     ux = (f * cx.view(1, 9, 1, 1)).sum(1) / rho
     uy = (f * cy.view(1, 9, 1, 1)).sum(1) / rho
     return 0.5 * ((ux - utx) ** 2 + (uy - uty) ** 2).mean()
+
+
+def _torch_population_loss(theta, f0, idx, target, tau, steps, F0, m):
+    """Eq. S13 on the nodes idx: post-collision populations of the last step."""
+    post, _ = _torch_unroll(theta, f0, tau, steps, F0, m)
+    flat = lambda a: a.permute(0, 2, 3, 1).reshape(-1, 9)
+    return ((flat(post)[idx.long()] - flat(target)[idx.long()]) ** 2).sum()
 
 
 def test_autograd_function_matches_torch_autograd_and_fd(lbm):
@@ -107,6 +122,44 @@ def test_autograd_function_matches_torch_autograd_and_fd(lbm):
     assert abs(fd - dd) <= 2e-2 * abs(dd) + 1e-9
 
 
+@pytest.mark.parametrize("form", ["population", "velocity_subset"])
+def test_subset_loss_autograd_matches_torch_autograd(lbm, form):
+    from paper_2403_18466_gb300.autograd import UnrolledLBM
+    B, n, steps, tau, F0, m = 2, 24, 6, 0.6, 1e-4, 1
+    f0 = torch.tensor(population_field(B, n, n, seed=75, neq=0.05), device=DEV)
+    theta0 = torch.tensor(inputs.xavier_mlp(9, bias_scale=0.3, gain=3.0, out_scale=0.01),
+                          dtype=torch.float32, device=DEV)
+    idx = torch.randperm(B * n * n, generator=torch.Generator().manual_seed(4))[:300]
+    idx[-1] = idx[0]
+    idx = idx.to(device=DEV, dtype=torch.int32)
+    run = UnrolledLBM(n, n, B, tau, steps, ckpt_every=4, force_amp=F0, force_mode=m, device=DEV)
+    theta = theta0.clone().requires_grad_(True)
+    f0g = f0.clone().requires_grad_(True)
+    theta_r = theta0.clone().requires_grad_(True)
+    f0_r = f0.clone().requires_grad_(True)
+    if form == "population":
+        target = f0 + torch.tensor(inputs.noise((B, 9, n, n), 76, 2e-3), dtype=torch.float32,
+                                   device=DEV)
+        loss = run.loss_subset(theta, f0g, idx, target_post=target)
+        loss_r = _torch_population_loss(theta_r, f0_r, idx, target, tau, steps, F0, m)
+    else:
+        utx = torch.tensor(inputs.noise((B, n, n), 77, 0.03), dtype=torch.float32, device=DEV)
+        uty = torch.tensor(inputs.noise((B, n, n), 78, 0.03), dtype=torch.float32, device=DEV)
+        loss = run.loss_subset(theta, f0g, idx, utx, uty)
+        _, f = _torch_unroll(theta_r, f0_r, tau, steps, F0, m)
+        rho = f.sum(1)
+        ux = (f * CX.to(DEV).view(1, 9, 1, 1)).sum(1) / rho
+        uy = (f * CY.to(DEV).view(1, 9, 1, 1)).sum(1) / rho
+        e = ((ux - utx) ** 2 + (uy - uty) ** 2).reshape(-1)[idx.long()]
+        loss_r = 0.5 * e.mean()
+    loss.backward()
+    loss_r.backward()
+    assert abs(loss.item() / loss_r.item() - 1) <= 1e-4
+    scale = theta_r.grad.abs().max().item()
+    assert (theta.grad - theta_r.grad).abs().max().item() <= 2e-4 * scale
+    assert (f0g.grad - f0_r.grad).abs().max().item() <= 2e-4 * f0_r.grad.abs().max().item()
+
+
 def test_data_generation_filter_and_targets(lbm):
     from paper_2403_18466_gb300 import data
     ds = data.generate(n=256, cg=8, trajectories=3, unroll=4, spinup=300, stride=64, seed=1)
@@ -123,6 +176,48 @@ def test_data_generation_filter_and_targets(lbm):
     ref = oracle.box_filter(lat.get_state().double().cpu().numpy(), 8)
     got = lat.box_filter(8).double().cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+    # population targets: streaming them gives back the filtered state whose
+    # velocity is the velocity target
+    for filt, d in (("box", ds), ("subsample", data.generate(n=256, cg=8, trajectories=2,
+                                                              unroll=4, spinup=300, stride=64,
+                                                              seed=1, filter="subsample"))):
+        assert d.target_post.shape == d.f0.shape and torch.isfinite(d.target_post).all()
+        c = lbm.Lattice(32, 32, d.f0.shape[0], device=DEV)
+        c.set_state(c.stream(d.target_post, 1))
+        _, vx, vy = c.moments()
+        assert (vx - d.utx).abs().max().item() <= 1e-6 and (vy - d.uty).abs().max().item() <= 1e-6
+    # the subsampled initial state is the DNS state at every 8th node: same first
+    # trajectory as a direct subsample of the same DNS after the same spin-up
+    dns = lbm.Lattice(256, 256, 1, tau=0.503, force_amp=1e-5, force_mode=4, device=DEV)
+    rho, ux, uy = inputs.random_velocity_field(256, 256, seed=1, k0=8.0, urms=0.02)
+    t = lambda a: torch.tensor(a[None], dtype=torch.float32, device=DEV)
+    dns.init_equilibrium(t(rho), t(ux), t(uy))
+    dns.step(300, "bgk")
+    f_dns = dns.get_state().cpu().numpy()
+    assert np.array_equal(d.f0[0:1].cpu().numpy(), f_dns[:, :, ::8, ::8])
+
+
+def test_paper_training_variant_reduces_population_loss(lbm):
+    """Subsampled data, |S| = 512 random nodes per epoch, population loss of
+    Eq. S13 after 4 unrolled steps: the all-node population loss drops."""
+    from paper_2403_18466_gb300 import data, train
+    from paper_2403_18466_gb300.autograd import UnrolledLBM
+    ds = data.generate(n=256, cg=8, trajectories=4, unroll=4, spinup=300, stride=64, seed=2,
+                       filter="subsample")
+    B, _, N, _ = ds.f0.shape
+    every = torch.arange(B * N * N, dtype=torch.int32, device=DEV)
+    run = UnrolledLBM(N, N, B, ds.tau_les, ds.unroll, 4, ds.force_les, ds.force_mode,
+                      device=DEV, precision="bf16")
+
+    def full_loss(theta):
+        with torch.no_grad():
+            return run.loss_subset(theta, ds.f0, every, target_post=ds.target_post).item()
+
+    theta0 = torch.tensor(inputs.xavier_mlp(3, out_scale=0.01), dtype=torch.float32, device=DEV)
+    theta, hist = train.train(ds, epochs=40, lr=3e-3, out_scale=0.01, verbose=False,
+                              precision="bf16", subset=512, loss="population")
+    assert np.all(np.isfinite(hist))
+    assert full_loss(theta) < full_loss(theta0)
 
 
 def test_short_training_run_reduces_loss(lbm):
