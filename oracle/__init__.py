@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the D2Q9 lattice-Boltzmann hot path.
+"""FP64 CPU oracle of the D2Q9 lattice-Boltzmann hot path (and, in
+``oracle.d3q19``, of the paper's D3Q19 setting).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``.  The library path never imports it.
@@ -22,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "d3q19_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 
@@ -51,10 +53,11 @@ def params(tau, smag_cs=0.0, smag_delta=1.0, force_amp=0.0, force_mode=0, hidden
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, IEEE FP64, no contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+               "-fno-fast-math", "-shared", "-fPIC", *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -76,6 +76,54 @@ def random_velocity_field(ny: int, nx: int, seed: int, k0: float = 8.0, urms: fl
     return np.ones((ny, nx)), ux, uy
 
 
+def random_velocity_field_3d(nz: int, ny: int, nx: int, seed: int, k0: float = 4.0,
+                             urms: float = 0.02):
+    """Seeded divergence-free 3D field: Gaussian random Fourier amplitudes with
+    |u_hat| shaped by sqrt(E(k) / (4 pi k^2)), E(k) ~ k^4 exp(-2 (k/k0)^2), made
+    solenoidal by removing the component along k, real part of the inverse FFT
+    (Nyquist planes dropped), zero mean, scaled so that
+    sqrt(<|u|^2> / 3) = urms.  Returns rho (ones), u [3, nz, ny, nx]."""
+    rng = np.random.default_rng(seed)
+    kz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
+    ky = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
+    kx = np.fft.fftfreq(nx, 1.0 / nx)[None, None, :]
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    k = np.sqrt(k2)
+    spec = k ** 4 * np.exp(-2.0 * (k / k0) ** 2)
+    amp = np.where(k > 0, np.sqrt(spec / (4 * np.pi * np.maximum(k2, 1))), 0.0)
+    w = (rng.standard_normal((3, nz, ny, nx)) + 1j * rng.standard_normal((3, nz, ny, nx))) * amp
+    kv = [np.broadcast_to(a, (nz, ny, nx)) for a in (kx, ky, kz)]
+    kdotw = sum(kv[a] * w[a] for a in range(3))
+    uh = np.stack([w[a] - kv[a] * kdotw / np.maximum(k2, 1) for a in range(3)])
+    for n, kk in ((nx, kv[0]), (ny, kv[1]), (nz, kv[2])):
+        if n % 2 == 0:
+            uh[:, np.abs(kk) == n // 2] = 0.0
+    u = np.real(np.fft.ifftn(uh, axes=(1, 2, 3)))
+    u -= u.mean(axis=(1, 2, 3), keepdims=True)
+    norm = np.sqrt(np.mean(np.sum(u ** 2, axis=0)) / 3.0)
+    if norm == 0.0:
+        raise ValueError("grid too small for a non-trivial solenoidal field")
+    u *= urms / norm
+    return np.ones((nz, ny, nx)), u
+
+
+def xavier_mlp_widths(seed: int, widths, bias_scale: float = 0.0, gain: float = 1.0,
+                      out_scale: float = 1.0):
+    """Seeded Xavier-uniform weights of a 19 -> widths... -> 19 MLP, packed as
+    W1[h1][19], b1, W2[h2][h1], b2, ..., W_out[19][h_last], b_out (float64)."""
+    rng = np.random.default_rng(seed)
+    dims = [19, *widths, 19]
+    parts = []
+    for layer, (nin, nout) in enumerate(zip(dims[:-1], dims[1:])):
+        lim = gain * np.sqrt(6.0 / (nin + nout))
+        Wl = rng.uniform(-lim, lim, (nout, nin))
+        bl = rng.uniform(-bias_scale, bias_scale, nout) if bias_scale else np.zeros(nout)
+        if layer == len(dims) - 2:
+            Wl, bl = Wl / gain * out_scale, bl * out_scale
+        parts += [Wl.ravel(), bl]
+    return np.concatenate(parts)
+
+
 def mlp_nparams(h: int = HIDDEN) -> int:
     return h * 9 + h + h * h + h + 9 * h + 9
 
