@@ -235,6 +235,7 @@ def run_gpu(args):
                          "ms_per_step": round(ms_step, 5), "hbm_gbs": roofline["achieved"],
                          "hbm_frac": roofline["frac"]}
     comps["training"] = _time_training(lbm, torch, dev, inputs)
+    comps["d3q19"] = _time_d3q19(lbm, torch, dev, inputs, hbm_peak)
     del lat
     torch.cuda.empty_cache()
 
@@ -321,6 +322,51 @@ def _time_training(lbm, torch, dev, inputs):
             "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
             "workspace_mb": round(ws.numel() * 4 / 2**20, 1)}
         del ws
+    return out
+
+
+def _time_d3q19(lbm, torch, dev, inputs, hbm_peak):
+    """The paper's 3D setting: D3Q19 BGK and Smagorinsky steps at 256^3
+    (152 B/node of algorithmic traffic) and the FP32 learned collision with the
+    paper's 19-300-300-100-19 network at 64^3."""
+    import numpy as np
+    out = {}
+    n = 256
+    # a 64^3 solenoidal field tiled 4 x 4 x 4 (periodic, still solenoidal)
+    rho, u = inputs.random_velocity_field_3d(64, 64, 64, seed=3, k0=4.0, urms=0.02)
+    rho, u = np.tile(rho, (4, 4, 4)), np.tile(u, (1, 4, 4, 4))
+    lat = lbm.Lattice3D(n, n, n, 1, tau=0.51, smag_cs=0.1, force_amp=1e-6, device=dev)
+    lat.init_equilibrium(torch.tensor(rho[None], dtype=torch.float32, device=dev),
+                         torch.tensor(u[None], dtype=torch.float32, device=dev))
+    del rho, u
+    stream = torch.cuda.current_stream(dev)
+    nodes = n ** 3
+    for kind, k in (("bgk", 50), ("smag", 50)):
+        lat.step(3, kind)
+        t = _time_steps(lat, kind, None, k, torch, stream)
+        g = 152 * nodes / (t / k * 1e-3) / 1e9
+        out[f"{kind}_256^3"] = {"mlups": round(nodes / (t / k * 1e-3) / 1e6, 1),
+                                "ms_per_step": round(t / k, 4), "hbm_gbs": round(g, 1),
+                                "hbm_frac": round(g / hbm_peak, 4)}
+    out["status"] = lbm.lbm_strerror(lat.status())
+    del lat
+    torch.cuda.empty_cache()
+    n = 64
+    rho, u = inputs.random_velocity_field_3d(n, n, n, seed=4, k0=4.0, urms=0.02)
+    lat = lbm.Lattice3D(n, n, n, 1, tau=0.6, device=dev)
+    lat.init_equilibrium(torch.tensor(rho[None], dtype=torch.float32, device=dev),
+                         torch.tensor(u[None], dtype=torch.float32, device=dev))
+    theta = torch.tensor(inputs.xavier_mlp_widths(5, (300, 300, 100), out_scale=0.01),
+                         dtype=torch.float32, device=dev)
+    w3 = lbm.weights3d_struct(theta)
+    lat.step(1, "mlp_f32", w3)
+    k = 5
+    t = _time_steps(lat, "mlp_f32", w3, k, torch, stream)
+    flop = 2 * (19 * 300 + 300 * 300 + 300 * 100 + 100 * 19)
+    out["mlp_f32_64^3"] = {"mlups": round(n ** 3 / (t / k * 1e-3) / 1e6, 1),
+                           "ms_per_step": round(t / k, 3),
+                           "mlp_tflops": round(flop * n ** 3 / (t / k * 1e-3) / 1e12, 2),
+                           "status": lbm.lbm_strerror(lat.status())}
     return out
 
 

@@ -37,6 +37,22 @@ class lbm_weights(C.Structure):
                 ("w3", C.c_void_p), ("b3", C.c_void_p), ("dtype", C.c_int)]
 
 
+class lbm3d_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("batch", C.c_int),
+                ("tau", C.c_double), ("smag_cs", C.c_double), ("smag_delta", C.c_double),
+                ("force_amp", C.c_double), ("force_mode", C.c_int), ("flags", C.c_int)]
+
+
+class lbm3d_weights(C.Structure):
+    _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("w4", C.c_void_p), ("b4", C.c_void_p),
+                ("dtype", C.c_int)]
+
+
+LBM3D_WIDTHS = (300, 300, 100)
+LBM3D_MLP_NPARAMS = 128319
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -72,6 +88,18 @@ _SIGS = {
     "lbm_structure_functions": (_i, [_vp, _i, _vp]),
     "lbm_energy_spectrum": (_i, [_vp, _i, _vp]),
     "lbm_strerror": (C.c_char_p, [_i]),
+    "lbm3d_mlp_nparams": (_sz, []),
+    "lbm3d_lattice": (None, [_vp, _vp, _vp, _vp]),
+    "lbm3d_init": (_i, [C.POINTER(_vp), C.POINTER(lbm3d_params), _vp, _vp, _vp]),
+    "lbm3d_destroy": (None, [_vp]),
+    "lbm3d_set_state": (_i, [_vp, _vp]),
+    "lbm3d_get_state": (_i, [_vp, _vp]),
+    "lbm3d_init_equilibrium": (_i, [_vp, _vp, _vp]),
+    "lbm3d_step": (_i, [_vp, _i, _i, C.POINTER(lbm3d_weights)]),
+    "lbm3d_moments": (_i, [_vp, _vp, _vp]),
+    "lbm3d_state_buffer": (_vp, [_vp]),
+    "lbm3d_status": (_i, [_vp]),
+    "lbm3d_clear_status": (_i, [_vp]),
 }
 
 
@@ -124,6 +152,37 @@ def weights_struct(theta):
     w = lbm_weights(*ptrs, dtype)
     w._keepalive = theta
     return w
+
+
+def make_params3d(nx, ny, nz, batch=1, tau=0.6, smag_cs=0.0, smag_delta=1.0, force_amp=0.0,
+                  force_mode=1):
+    return lbm3d_params(int(nx), int(ny), int(nz), int(batch), float(tau), float(smag_cs),
+                        float(smag_delta), float(force_amp), int(force_mode), 0)
+
+
+def weights3d_struct(theta):
+    """lbm3d_weights viewing a packed FP32 parameter tensor of the paper's network
+    (LBM3D_MLP_NPARAMS elements: w1[300][19], b1, w2[300][300], b2, w3[100][300],
+    b3, w4[19][100], b4) on the device."""
+    import torch
+    assert theta.is_contiguous() and theta.numel() == LBM3D_MLP_NPARAMS
+    dtype = {torch.float32: 0, torch.bfloat16: 1}[theta.dtype]
+    h1, h2, h3 = LBM3D_WIDTHS
+    sizes = [h1 * 19, h1, h2 * h1, h2, h3 * h2, h3, 19 * h3, 19]
+    base, es, off, ptrs = theta.data_ptr(), theta.element_size(), 0, []
+    for n in sizes:
+        ptrs.append(base + off * es)
+        off += n
+    w = lbm3d_weights(*ptrs, dtype)
+    w._keepalive = theta
+    return w
+
+
+def lbm3d_lattice():
+    """(cx, cy, cz, w) as compiled into the D3Q19 kernels (host call, no GPU)."""
+    cx, cy, cz, w = (C.c_int * 19)(), (C.c_int * 19)(), (C.c_int * 19)(), (C.c_float * 19)()
+    load().lbm3d_lattice(C.cast(cx, _vp), C.cast(cy, _vp), C.cast(cz, _vp), C.cast(w, _vp))
+    return list(cx), list(cy), list(cz), list(w)
 
 
 def lbm_record_bytes(params, n, ckpt_every):
@@ -185,7 +244,7 @@ class Lattice:
         for b in self.bufs:
             if b.data_ptr() == p:
                 return b
-        raise LbmError("state buffer is not one of this lattice's tensors")
+        raise LbmError(LBM_ERR_ARG, "lbm_state_buffer")
 
     # -- stepping -----------------------------------------------------------
     def step(self, n, kind="bgk", weights=None):
@@ -295,3 +354,77 @@ class Lattice:
         w = C.byref(weights) if weights is not None else None
         _check(self.lib.lbm_run_host(self.ctx, _ptr(f_pre_host), int(n), k, w, _ptr(rho),
                                      _ptr(ux), _ptr(uy)), "lbm_run_host")
+
+
+class Lattice3D:
+    """A D3Q19 context (include/lbm3d.h) over two torch-owned state buffers.
+
+    Methods mirror the C entry points (lbm3d_set_state -> set_state, ...)."""
+
+    def __init__(self, nx, ny, nz, batch=1, tau=0.6, smag_cs=0.0, smag_delta=1.0, force_amp=0.0,
+                 force_mode=1, stream=None, device="cuda"):
+        import torch
+        self.lib = load()
+        self.params = make_params3d(nx, ny, nz, batch, tau, smag_cs, smag_delta, force_amp,
+                                    force_mode)
+        self.shape = (batch, 19, nz, ny, nx)
+        self.device = torch.device(device)
+        self.bufs = [torch.zeros(self.shape, dtype=torch.float32, device=self.device)
+                     for _ in range(2)]
+        self.cuda_stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = C.c_void_p()
+        _check(self.lib.lbm3d_init(C.byref(ctx), C.byref(self.params), _ptr(self.bufs[0]),
+                                   _ptr(self.bufs[1]), C.c_void_p(self.cuda_stream.cuda_stream)),
+               "lbm3d_init")
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm3d_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def set_state(self, f_pre):
+        assert tuple(f_pre.shape) == self.shape and f_pre.is_contiguous()
+        _check(self.lib.lbm3d_set_state(self.ctx, _ptr(f_pre)), "lbm3d_set_state")
+
+    def get_state(self, out=None):
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float32, device=self.device) if out is None \
+            else out
+        _check(self.lib.lbm3d_get_state(self.ctx, _ptr(out)), "lbm3d_get_state")
+        return out
+
+    def init_equilibrium(self, rho, u):
+        _check(self.lib.lbm3d_init_equilibrium(self.ctx, _ptr(rho), _ptr(u)),
+               "lbm3d_init_equilibrium")
+
+    def step(self, n, kind="bgk", weights=None):
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        w = C.byref(weights) if weights is not None else None
+        _check(self.lib.lbm3d_step(self.ctx, int(n), k, w), "lbm3d_step")
+
+    def moments(self):
+        import torch
+        B, _, nz, ny, nx = self.shape
+        rho = torch.empty((B, nz, ny, nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((B, 3, nz, ny, nx), dtype=torch.float32, device=self.device)
+        _check(self.lib.lbm3d_moments(self.ctx, _ptr(rho), _ptr(u)), "lbm3d_moments")
+        return rho, u
+
+    def state_buffer(self):
+        return self.lib.lbm3d_state_buffer(self.ctx)
+
+    def state_tensor(self):
+        p = self.state_buffer()
+        for b in self.bufs:
+            if b.data_ptr() == p:
+                return b
+        raise LbmError(LBM_ERR_ARG, "lbm3d_state_buffer")
+
+    def status(self):
+        return self.lib.lbm3d_status(self.ctx)
+
+    def clear_status(self):
+        _check(self.lib.lbm3d_clear_status(self.ctx), "lbm3d_clear_status")

@@ -16,7 +16,7 @@ def _declared():
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+            names |= set(re.findall(r"\b(lbm(?:3d)?_\w+)\s*\(", src))
     return names
 
 
@@ -29,7 +29,8 @@ def lib():
 
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
-    assert {"lbm_init", "lbm_step", "lbm_moments", "lbm_backward"} <= names
+    assert {"lbm_init", "lbm_step", "lbm_moments", "lbm_backward", "lbm3d_init",
+            "lbm3d_step"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), n
 
@@ -63,3 +64,35 @@ def test_record_bytes_and_strerror(lib):
     for code in (0, -1, -2, -3, -4, -5):
         assert lbm.lbm_strerror(code)
     assert lbm.lbm_strerror(-99) == "unknown error"
+
+
+def test_d3q19_tables_match_the_oracle(lib):
+    """The stencil compiled into the D3Q19 kernels equals the oracle's copy of
+    the paper's table (host call, no GPU)."""
+    import numpy as np
+    import oracle.d3q19 as o3
+    from paper_2403_18466_gb300 import lbm
+    cx, cy, cz, w = lbm.lbm3d_lattice()
+    ocx, ocy, ocz, ow = o3.lattice()
+    assert list(ocx) == cx and list(ocy) == cy and list(ocz) == cz
+    assert np.array_equal(np.float32(ow), np.array(w, dtype=np.float32))
+    assert lib.lbm3d_mlp_nparams() == o3.mlp_nparams() == lbm.LBM3D_MLP_NPARAMS
+
+
+def test_d3q19_host_side_argument_errors(lib):
+    from paper_2403_18466_gb300 import lbm
+    ctx = C.c_void_p()
+    p = lbm.make_params3d(8, 8, 8, tau=0.6)
+    assert lib.lbm3d_init(C.byref(ctx), None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_init(C.byref(ctx), C.byref(p), None, None, None) == lbm.LBM_ERR_ARG
+    for bad in (lbm.make_params3d(8, 8, 8, tau=0.5), lbm.make_params3d(8, 0, 8),
+                lbm.make_params3d(8, 70000, 1), lbm.make_params3d(8, 8, 300, batch=300)):
+        assert lib.lbm3d_init(C.byref(ctx), C.byref(bad), C.c_void_p(256), C.c_void_p(512),
+                              None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_init(C.byref(ctx), C.byref(p), C.c_void_p(256), C.c_void_p(256),
+                          None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_step(None, 1, 0, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_moments(None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_status(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm3d_state_buffer(None) is None
+    lib.lbm3d_destroy(None)

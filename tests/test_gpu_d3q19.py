@@ -1,0 +1,149 @@
+"""GPU parity of the paper's D3Q19 setting (include/lbm3d.h) against the FP64
+D3Q19 oracle, through the C ABI.
+
+Tolerances (FP32 kernels): one step of BGK / Smagorinsky / the FP32 learned
+collision with the paper's 19-300-300-100-19 network: 1e-5 of each weight w_i
+(max |df_i| / w_i); 200 BGK steps with the sine forcing: 1e-5 relative per
+population; conserved moments per node to FP32 rounding.  The oracle starts
+from the GPU's own FP32 input state.  Shapes cover ragged x rows (nx not a
+multiple of the 128-thread block or of the 32-node MLP tile), batches, and the
+1 x 1 x 1 lattice.
+"""
+import numpy as np
+import pytest
+
+import oracle.d3q19 as o3
+from paper_2403_18466_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+_, _, _, W = o3.lattice()
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2403_18466_gb300 import lbm as m
+    m.load()
+    return m
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=DEV)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def field3d(B, nz, ny, nx, seed, urms=0.03, neq=0.01, mean_u=(0.01, -0.005, 0.007)):
+    """Seeded FP32 pre-collision D3Q19 populations: feq of a solenoidal field
+    plus a mean flow (on grids too small for a random field, the mean flow
+    alone), with a multiplicative non-equilibrium part."""
+    out = np.empty((B, 19, nz, ny, nx))
+    for b in range(B):
+        try:
+            rho, u = inputs.random_velocity_field_3d(nz, ny, nx, seed=seed + b, k0=2.0, urms=urms)
+        except ValueError:
+            rho, u = np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx))
+        u = u + np.array(mean_u)[:, None, None, None]
+        rho = rho * (1.0 + inputs.noise(rho.shape, seed + 100 + b, 0.01))
+        out[b] = o3.equilibrium_field(rho[None], u[None])[0]
+    out *= 1.0 + inputs.noise(out.shape, seed + 200, neq)
+    return out.astype(np.float32)
+
+
+def wpe(a, ref):
+    return float(np.max(np.abs(a - ref) / W[None, :, None, None, None]))
+
+
+SHAPES = [(16, 12, 10, 1), (37, 5, 3, 2), (130, 3, 2, 1), (1, 1, 1, 1), (64, 8, 4, 1)]
+
+
+@pytest.mark.parametrize("kind", ["bgk", "smag"])
+@pytest.mark.parametrize("nx,ny,nz,B", SHAPES)
+def test_one_step_parity(lbm, kind, nx, ny, nz, B):
+    tau, cs, F, m = 0.53, 0.3, 2e-4, 1
+    f = field3d(B, nz, ny, nx, seed=11, neq=0.03)
+    lat = lbm.Lattice3D(nx, ny, nz, B, tau=tau, smag_cs=cs, force_amp=F, force_mode=m,
+                        device=DEV)
+    lat.set_state(_dev(f))
+    g = o3.stream_push(_np(lat.get_state()))
+    lat.step(1, kind)
+    k = o3.BGK if kind == "bgk" else o3.SMAG
+    ref = o3.stream_pull(o3.step(k, g, o3.params(tau, smag_cs=cs, force_amp=F, force_mode=m)))
+    got = _np(lat.get_state())
+    assert wpe(got, ref) <= 1e-5
+    assert lat.status() == lbm.LBM_OK
+
+
+def test_bgk_200_steps_with_forcing(lbm):
+    n, tau, F = 12, 0.6, 1e-5
+    rho, u = inputs.random_velocity_field_3d(n, n, n, seed=5, k0=2.0, urms=0.02)
+    lat = lbm.Lattice3D(n, n, n, 1, tau=tau, force_amp=F, force_mode=1, device=DEV)
+    lat.init_equilibrium(_dev(rho[None]), _dev(u[None]))
+    f0 = lat.get_state()
+    g = o3.stream_push(_np(f0))
+    lat.step(200, "bgk")
+    g = o3.run(o3.BGK, g, 200, o3.params(tau, force_amp=F, force_mode=1))
+    got, ref = _np(lat.get_state()), o3.stream_pull(g)
+    assert float(np.max(np.abs(got - ref) / np.abs(ref))) <= 1e-5
+    assert abs(got.sum() / _np(f0).sum() - 1) <= 1e-6
+    assert lat.status() == lbm.LBM_OK
+
+
+def test_moments_and_equilibrium_init(lbm):
+    nx, ny, nz = 20, 6, 5
+    rho, u = inputs.random_velocity_field_3d(nz, ny, nx, seed=8, k0=2.0, urms=0.03)
+    rho = rho * (1 + inputs.noise(rho.shape, 9, 0.01))
+    lat = lbm.Lattice3D(nx, ny, nz, 1, device=DEV)
+    lat.init_equilibrium(_dev(rho[None]), _dev(u[None]))
+    r, v = lat.moments()
+    assert np.allclose(_np(r)[0], rho, rtol=2e-6, atol=0)
+    assert np.allclose(_np(v)[0], u, rtol=0, atol=2e-6 * np.abs(u).max() + 1e-9)
+    ref = o3.equilibrium_field(np.float32(rho)[None].astype(float), np.float32(u)[None].astype(float))
+    assert wpe(_np(lat.get_state()), ref) <= 1e-6
+
+
+def _weights(seed, out_scale=0.002):
+    return inputs.xavier_mlp_widths(seed, (300, 300, 100), bias_scale=0.1, gain=1.5,
+                                    out_scale=out_scale)
+
+
+@pytest.mark.parametrize("nx,ny,nz,B", [(16, 4, 3, 2), (37, 3, 2, 1), (1, 1, 1, 1), (64, 2, 2, 1)])
+def test_mlp_f32_one_step_parity(lbm, nx, ny, nz, B):
+    tau, F = 0.6, 2e-4
+    theta = _weights(21)
+    f = field3d(B, nz, ny, nx, seed=31, neq=0.02)
+    lat = lbm.Lattice3D(nx, ny, nz, B, tau=tau, force_amp=F, force_mode=1, device=DEV)
+    lat.set_state(_dev(f))
+    g = o3.stream_push(_np(lat.get_state()))
+    th = torch.tensor(theta, dtype=torch.float32, device=DEV)
+    lat.step(1, "mlp_f32", lbm.weights3d_struct(th))
+    ref = o3.stream_pull(o3.step(o3.MLP, g, o3.params(tau, force_amp=F, force_mode=1),
+                                 np.float32(theta).astype(float)))
+    got = _np(lat.get_state())
+    assert wpe(got, ref) <= 1e-5
+    # the correction is really there (the test would pass with BGK otherwise)
+    bgk = o3.stream_pull(o3.step(o3.BGK, g, o3.params(tau, force_amp=F, force_mode=1)))
+    assert wpe(ref, bgk) > 100 * wpe(got, ref)
+    # conservation per node: the post-collision populations (state + w) carry
+    # the input's mass and momentum (plus the force)
+    fin = o3.stream_pull(g)
+    post = _np(lat.state_tensor()) + np.float32(W).astype(float)[None, :, None, None, None]
+    C = np.stack(o3.lattice()[:3], 1).astype(float)
+    assert np.abs(post.sum(1) - fin.sum(1)).max() <= 2e-6
+    dj = np.einsum("bizyx,ia->bazyx", post - fin, C)
+    assert np.abs(dj).max() <= 2e-4 + 2e-6   # |F| <= 2e-4 per node
+    assert lat.status() == lbm.LBM_OK
+
+
+def test_unsupported_and_bad_weights(lbm):
+    lat = lbm.Lattice3D(8, 8, 8, 1, device=DEV)
+    with pytest.raises(lbm.LbmError):
+        lat.step(1, "mlp_f32", None)
+    th = torch.zeros(lbm.LBM3D_MLP_NPARAMS, dtype=torch.bfloat16, device=DEV)
+    with pytest.raises(lbm.LbmError):
+        lat.step(1, "mlp_f32", lbm.weights3d_struct(th))
