@@ -367,6 +367,26 @@ def _time_d3q19(lbm, torch, dev, inputs, hbm_peak):
                            "ms_per_step": round(t / k, 3),
                            "mlp_tflops": round(flop * n ** 3 / (t / k * 1e-3) / 1e12, 2),
                            "status": lbm.lbm_strerror(lat.status())}
+    del lat
+    torch.cuda.empty_cache()
+    # tensor-core collision at 256^3 (the 64^3 field tiled, as above)
+    n = 256
+    rho, u = inputs.random_velocity_field_3d(64, 64, 64, seed=4, k0=4.0, urms=0.02)
+    rho, u = np.tile(rho, (4, 4, 4)), np.tile(u, (1, 4, 4, 4))
+    lat = lbm.Lattice3D(n, n, n, 1, tau=0.6, force_amp=1e-6, device=dev)
+    lat.init_equilibrium(torch.tensor(rho[None], dtype=torch.float32, device=dev),
+                         torch.tensor(u[None], dtype=torch.float32, device=dev))
+    del rho, u
+    lat.step(3, "mlp_bf16", w3)
+    k = 20
+    t = _time_steps(lat, "mlp_bf16", w3, k, torch, stream)
+    rate = n ** 3 / (t / k * 1e-3)
+    _, tc_peak, _ = _peaks()
+    out["mlp_bf16_256^3"] = {"mlups": round(rate / 1e6, 1), "ms_per_step": round(t / k, 4),
+                             "mlp_tflops": round(flop * rate / 1e12, 1),
+                             "tensor_frac": round(flop * rate / 1e12 / tc_peak, 4),
+                             "flop_per_node": flop,
+                             "status": lbm.lbm_strerror(lat.status())}
     return out
 
 

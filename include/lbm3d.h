@@ -87,9 +87,15 @@ int lbm3d_get_state(lbm3d_ctx *ctx, float *f_pre);
 int lbm3d_init_equilibrium(lbm3d_ctx *ctx, const float *rho, const float *u);
 
 /* Advance n >= 0 steps: pull-stream (Eq. S2), collide with `kind`, EDM force,
- * store.  LBM_MLP_F32 needs FP32 weights; LBM_MLP_BF16 is the tensor-core
- * collision (LBM_ERR_UNSUPPORTED where not built).  A node reaching
- * |u| >= 0.4 or a non-finite value sets the sticky status flag. */
+ * store.  Both learned kinds take FP32 weights (dtype 0):
+ *   LBM_MLP_F32   the network in FP32 on the CUDA cores;
+ *   LBM_MLP_BF16  the network on the tensor cores (tcgen05): weights, biases
+ *                 and activations rounded to bf16, FP32 accumulation; the
+ *                 populations, equilibrium, conservation layer and update
+ *                 stay FP32.  The first call allocates a 286 KB device copy of
+ *                 the weights in operand layout, refreshed at every call.
+ * A node reaching |u| >= 0.4 or a non-finite value sets the sticky status
+ * flag; a device wait that gives up sets LBM_ERR_TIMEOUT. */
 int lbm3d_step(lbm3d_ctx *ctx, int n, lbm_collision kind, const lbm3d_weights *w);
 
 /* rho and u = j/rho of the current pre-collision populations (either NULL). */

@@ -33,6 +33,16 @@ size_t mlp_f32_smem_bytes();
 cudaError_t launch_step_mlp_f32(const Grid3 &g, const float *in, float *out, const Collide3 &c,
                                 const Mlp3 &w, int *flag, cudaStream_t s);
 cudaError_t launch_set_state(const Grid3 &g, const float *f_pre, float *state, cudaStream_t s);
+
+// d3q19_mlp_tc.cu: the tensor-core learned collision.  The FP32 weights are
+// first laid out as BF16 operand tiles in a device buffer of
+// mlp_tc_weight_bytes() bytes (launch_prepare_weights_tc), which the step
+// kernel reads (resident W1/W4, streamed W2/W3).  One persistent CTA per SM.
+size_t mlp_tc_weight_bytes();
+cudaError_t launch_prepare_weights_tc(const Mlp3 &w, void *gw, cudaStream_t s);
+cudaError_t launch_step_mlp_tc(const Grid3 &g, const float *in, float *out, const Collide3 &c,
+                               const void *gw, int sms, int *flag, int *timeout_flag,
+                               cudaStream_t s);
 cudaError_t launch_get_state(const Grid3 &g, const float *state, float *f_pre, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const Grid3 &g, const float *rho, const float *u,
                                     float *state, cudaStream_t s);

@@ -23,6 +23,8 @@ struct lbm3d_ctx {
   Collide3 cp;
   int *d_flag;     // [0] unstable, [1] device wait timeout
   float *d_force;  // ny + nz + nx floats (F_x(y), F_y(z), F_z(x)), or nullptr
+  void *d_wtc;     // BF16 operand tiles of the tensor-core collision (first use)
+  int sms;
 };
 
 namespace {
@@ -46,8 +48,7 @@ bool bad_params(const lbm3d_params *p) {
 
 int check_weights(lbm_collision kind, const lbm3d_weights *w) {
   if (kind == LBM_BGK || kind == LBM_SMAG) return LBM_OK;
-  if (kind == LBM_MLP_BF16) return LBM_ERR_UNSUPPORTED;
-  if (kind != LBM_MLP_F32) return LBM_ERR_ARG;
+  if (kind != LBM_MLP_F32 && kind != LBM_MLP_BF16) return LBM_ERR_ARG;
   if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || !w->w4 || !w->b4)
     return LBM_ERR_ARG;
   if (w->dtype != 0) return LBM_ERR_UNSUPPORTED;
@@ -98,6 +99,12 @@ int lbm3d_init(lbm3d_ctx **out, const lbm3d_params *p, float *b0, float *b1, voi
   c->cp.tau0_sq = (float)(p->tau * p->tau);
   c->cp.smag_c18 = (float)(18.0 * (p->smag_cs * p->smag_delta) * (p->smag_cs * p->smag_delta));
   c->cp.fx_y = c->cp.fy_z = c->cp.fz_x = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return LBM_ERR_CUDA;
+  }
   if (cudaMalloc(&c->d_flag, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(c->d_flag, 0, 2 * sizeof(int)) != cudaSuccess) {
     cudaFree(c->d_flag);
@@ -134,6 +141,7 @@ void lbm3d_destroy(lbm3d_ctx *c) {
   cudaStreamSynchronize(c->stream);
   cudaFree(c->d_flag);
   cudaFree(c->d_force);
+  cudaFree(c->d_wtc);
   delete c;
 }
 
@@ -159,10 +167,17 @@ int lbm3d_step(lbm3d_ctx *c, int n, lbm_collision kind, const lbm3d_weights *w) 
   if (!c || n < 0) return LBM_ERR_ARG;
   const int wc = check_weights(kind, w);
   if (wc != LBM_OK) return wc;
+  if (kind == LBM_MLP_BF16 && n > 0) {
+    if (!c->d_wtc) CUDA_TRY(cudaMalloc(&c->d_wtc, lbm::d3::mlp_tc_weight_bytes()));
+    CUDA_TRY(lbm::d3::launch_prepare_weights_tc(f32_view(w), c->d_wtc, c->stream));
+  }
   for (int s = 0; s < n; ++s) {
     const float *in = c->buf[c->cur];
     float *out = c->buf[c->cur ^ 1];
-    if (kind == LBM_MLP_F32)
+    if (kind == LBM_MLP_BF16)
+      CUDA_TRY(lbm::d3::launch_step_mlp_tc(c->g, in, out, c->cp, c->d_wtc, c->sms, c->d_flag,
+                                           c->d_flag + 1, c->stream));
+    else if (kind == LBM_MLP_F32)
       CUDA_TRY(lbm::d3::launch_step_mlp_f32(c->g, in, out, c->cp, f32_view(w), c->d_flag,
                                             c->stream));
     else

@@ -145,5 +145,140 @@ def test_unsupported_and_bad_weights(lbm):
     with pytest.raises(lbm.LbmError):
         lat.step(1, "mlp_f32", None)
     th = torch.zeros(lbm.LBM3D_MLP_NPARAMS, dtype=torch.bfloat16, device=DEV)
-    with pytest.raises(lbm.LbmError):
-        lat.step(1, "mlp_f32", lbm.weights3d_struct(th))
+    for kind in ("mlp_f32", "mlp_bf16"):
+        with pytest.raises(lbm.LbmError):
+            lat.step(1, kind, lbm.weights3d_struct(th))
+        with pytest.raises(lbm.LbmError):
+            lat.step(1, kind, None)
+
+
+# ---------------------------------------------------------------------------
+# The tensor-core learned collision (LBM_MLP_BF16 on D3Q19).
+# ---------------------------------------------------------------------------
+def _bf(a):
+    import torch as T
+    return T.tensor(np.asarray(a, dtype=np.float64)).to(T.bfloat16).double().numpy()
+
+
+def _unpack(theta):
+    sizes = [(300, 19), (300,), (300, 300), (300,), (100, 300), (100,), (19, 100), (19,)]
+    out, off = [], 0
+    for s in sizes:
+        n = int(np.prod(s))
+        out.append(np.asarray(theta[off:off + n], dtype=np.float64).reshape(s))
+        off += n
+    return out
+
+
+def _force_nodes(B, nz, ny, nx, F, m):
+    """Per-node force of the sine forcing in node order (b, z, y, x), via the oracle."""
+    prm = o3.params(0.6, force_amp=F, force_mode=m)
+    Fz = np.array([o3.force(prm, z, 0, 0, nz, ny, nx)[1] for z in range(nz)])
+    Fy = np.array([o3.force(prm, 0, y, 0, nz, ny, nx)[0] for y in range(ny)])
+    Fx = np.array([o3.force(prm, 0, 0, x, nz, ny, nx)[2] for x in range(nx)])
+    fx = np.broadcast_to(Fy[None, None, :, None], (B, nz, ny, nx)).reshape(-1)
+    fy = np.broadcast_to(Fz[None, :, None, None], (B, nz, ny, nx)).reshape(-1)
+    fz = np.broadcast_to(Fx[None, None, None, :], (B, nz, ny, nx)).reshape(-1)
+    return np.stack([fx, fy, fz], 1)
+
+
+def emulate_tc_step(g, theta, tau, F, m, round_acts=True):
+    """Test-side numpy restatement of one learned D3Q19 step with the roundings
+    of the tensor-core path: weights, biases, the input x and the hidden
+    activations rounded to bf16, sums in FP64.  With round_acts=False only the
+    parameters are rounded.  g: stored post-collision state (FP64)."""
+    B, _, nz, ny, nx = g.shape
+    cx, cy, cz, w = o3.lattice()
+    C = np.stack([cx, cy, cz], 1).astype(float)
+    f = o3.stream_pull(g)
+    fn = f.transpose(0, 2, 3, 4, 1).reshape(-1, 19)
+    rho = fn.sum(1)
+    u = (fn @ C) / rho[:, None]
+
+    def feq(r, v):
+        cu = v @ C.T
+        return w[None] * r[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (v * v).sum(1)[:, None])
+
+    fe = feq(rho, u)
+    rnd = _bf if round_acts else (lambda a: a)
+    W1, b1, W2, b2, W3, b3, W4, b4 = [_bf(p) for p in _unpack(theta)]
+    lr = lambda a: np.where(a >= 0, a, 0.01 * a)
+    x = rnd((fn - fe) / rho[:, None])
+    h1 = rnd(lr(x @ W1.T + b1))
+    h2 = rnd(lr(h1 @ W2.T + b2))
+    h3 = rnd(lr(h2 @ W3.T + b3))
+    o = h3 @ W4.T + b4
+    oh = o - o.sum(1, keepdims=True) / 19 - sum(np.outer(o @ C[:, a], C[:, a]) / 10 for a in range(3))
+    Fn = _force_nodes(B, nz, ny, nx, F, m)
+    post = fn + (fe - fn) / tau + (rho / tau)[:, None] * oh + feq(rho, u + Fn / rho[:, None]) - fe
+    post = post.reshape(B, nz, ny, nx, 19).transpose(0, 4, 1, 2, 3)
+    return o3.stream_pull(post)
+
+
+@pytest.mark.parametrize("nx,ny,nz,B", [(130, 3, 2, 1), (37, 5, 3, 2), (1, 1, 1, 1),
+                                        (256, 16, 16, 1)])
+def test_mlp_tc_one_step_parity(lbm, nx, ny, nz, B):
+    """Against the bf16-rounding restatement: within 5e-3 of the learned
+    correction's size (only FP32-vs-FP64 sums and rare one-ulp bf16 decisions
+    differ); against the restatement without activation rounding (bf16
+    parameters only): within 5e-2 of it."""
+    tau, F, m = 0.6, 2e-4, 1
+    theta = _weights(23, out_scale=0.01)
+    f = field3d(B, nz, ny, nx, seed=41, neq=0.03)
+    lat = lbm.Lattice3D(nx, ny, nz, B, tau=tau, force_amp=F, force_mode=m, device=DEV)
+    lat.set_state(_dev(f))
+    g = o3.stream_push(_np(lat.get_state()))
+    th = torch.tensor(theta, dtype=torch.float32, device=DEV)
+    lat.step(1, "mlp_bf16", lbm.weights3d_struct(th))
+    got = _np(lat.get_state())
+    assert lat.status() == lbm.LBM_OK
+    th32 = np.float32(theta).astype(float)
+    emu = emulate_tc_step(g, th32, tau, F, m)
+    bgk = o3.stream_pull(o3.step(o3.BGK, g, o3.params(tau, force_amp=F, force_mode=m)))
+    corr = wpe(emu, bgk)
+    assert corr > 1e-4
+    assert wpe(got, emu) <= 5e-3 * corr + 1e-6
+    ref = emulate_tc_step(g, th32, tau, F, m, round_acts=False)
+    assert wpe(got, ref) <= 5e-2 * corr
+    if B * nx * ny * nz <= 2000:
+        # the plain oracle (FP64 network, bf16-rounded parameters) agrees with the restatement
+        wb = np.concatenate([_bf(p).ravel() for p in _unpack(th32)])
+        ora = o3.stream_pull(o3.step(o3.MLP, g, o3.params(tau, force_amp=F, force_mode=m), wb))
+        assert wpe(ora, ref) <= 1e-9
+
+
+def test_mlp_tc_zero_output_layer_is_bgk(lbm):
+    nx, ny, nz, B = 64, 4, 4, 1
+    theta = _weights(24)
+    theta[-(19 * 100 + 19):] = 0.0
+    f = field3d(B, nz, ny, nx, seed=43, neq=0.03)
+    lat = lbm.Lattice3D(nx, ny, nz, B, tau=0.6, force_amp=1e-4, device=DEV)
+    lat.set_state(_dev(f))
+    lat.step(1, "mlp_bf16", lbm.weights3d_struct(torch.tensor(theta, dtype=torch.float32,
+                                                                 device=DEV)))
+    tc = _np(lat.get_state())
+    ref = lbm.Lattice3D(nx, ny, nz, B, tau=0.6, force_amp=1e-4, device=DEV)
+    ref.set_state(_dev(f))
+    ref.step(1, "bgk")
+    assert wpe(tc, _np(ref.get_state())) <= 1e-6
+
+
+def test_mlp_tc_many_steps_agree_with_fp32_collision(lbm):
+    """20 steps, several tiles per CTA: the tensor-core and FP32 learned
+    collisions stay within the bf16 error of the correction."""
+    n, B = 48, 1
+    theta = torch.tensor(_weights(25, out_scale=0.0005), dtype=torch.float32, device=DEV)
+    w = lbm.weights3d_struct(theta)
+    f = _dev(field3d(B, n, n, n, seed=44, neq=0.02))
+    a = lbm.Lattice3D(n, n, n, B, tau=0.6, force_amp=1e-5, device=DEV)
+    b = lbm.Lattice3D(n, n, n, B, tau=0.6, force_amp=1e-5, device=DEV)
+    c = lbm.Lattice3D(n, n, n, B, tau=0.6, force_amp=1e-5, device=DEV)
+    for lat in (a, b, c):
+        lat.set_state(f)
+    a.step(20, "mlp_bf16", w)
+    b.step(20, "mlp_f32", w)
+    c.step(20, "bgk")
+    fa, fb, fc = _np(a.get_state()), _np(b.get_state()), _np(c.get_state())
+    assert a.status() == lbm.LBM_OK and b.status() == lbm.LBM_OK
+    assert wpe(fb, fc) > 1e-5
+    assert wpe(fa, fb) <= 5e-2 * wpe(fb, fc)
