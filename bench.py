@@ -492,6 +492,22 @@ def run_profile_case(args):
     from paper_2403_18466_gb300 import inputs, lbm
     dev = torch.device("cuda:0")
     lbm.load()
+    if args.profile.startswith("d3_"):
+        # D3Q19 (the paper's 3D setting) on a --grid^3 lattice
+        kind, n = args.profile[3:], args.grid
+        rho, u = inputs.random_velocity_field_3d(n, n, n, seed=4, k0=4.0, urms=0.02)
+        lat = lbm.Lattice3D(n, n, n, 1, tau=0.6, force_amp=1e-6, device=dev)
+        lat.init_equilibrium(torch.tensor(rho[None], dtype=torch.float32, device=dev),
+                             torch.tensor(u[None], dtype=torch.float32, device=dev))
+        theta = torch.tensor(inputs.xavier_mlp_widths(5, (300, 300, 100), out_scale=0.01),
+                             dtype=torch.float32, device=dev)
+        lat.step(args.steps, kind, lbm.weights3d_struct(theta))
+        torch.cuda.synchronize()
+        rc = lat.status()
+        print(f"profile case {args.profile} {n}^3 x {args.steps}: {lbm.lbm_strerror(rc)}")
+        if rc != lbm.LBM_OK:
+            sys.exit(1)
+        return
     lat = _initial_state(lbm, torch, dev, n=args.grid)
     theta = torch.tensor(inputs.xavier_mlp(3, out_scale=OUT_SCALE), dtype=torch.float32,
                          device=dev)
@@ -532,7 +548,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", default=None, choices=["bgk", "smag", "mlp_bf16", "mlp_f32"],
+    ap.add_argument("--profile", default=None,
+                    choices=["bgk", "smag", "mlp_bf16", "mlp_f32", "d3_bgk", "d3_smag",
+                             "d3_mlp_bf16", "d3_mlp_f32"],
                     help="run a small case of one kernel for ncu and exit")
     ap.add_argument("--grid", type=int, default=2048)
     args = ap.parse_args()

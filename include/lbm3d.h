@@ -92,8 +92,10 @@ int lbm3d_init_equilibrium(lbm3d_ctx *ctx, const float *rho, const float *u);
  *   LBM_MLP_BF16  the network on the tensor cores (tcgen05): weights, biases
  *                 and activations rounded to bf16, FP32 accumulation; the
  *                 populations, equilibrium, conservation layer and update
- *                 stay FP32.  The first call allocates a 286 KB device copy of
- *                 the weights in operand layout, refreshed at every call.
+ *                 stay FP32.  The first call allocates 4.6 MB of device
+ *                 copies of the weights in operand layout (replicated so that
+ *                 the SMs streaming them spread over the L2 cache), refreshed
+ *                 at every call.
  * A node reaching |u| >= 0.4 or a non-finite value sets the sticky status
  * flag; a device wait that gives up sets LBM_ERR_TIMEOUT. */
 int lbm3d_step(lbm3d_ctx *ctx, int n, lbm_collision kind, const lbm3d_weights *w);

@@ -15,26 +15,38 @@
 //   L4  [128 x 112] x [112 x  32]   K = 100 + 1 + 11 zeros; N = 19 + 13 zero rows
 // N = 304 exceeds one MMA, so L1 and L2 issue two MMAs per K step (N = 160, 144).
 //
-// The paper's network has 280 KB of BF16 weights, more than an SM's shared
-// memory, so W1 and W4 stay resident and W2 and W3 are streamed every tile in
-// K chunks of 32 (19,456 / 7,168 bytes) through a 6-slot ring filled by bulk
-// copies (cp.async.bulk) from a pre-laid-out copy in global memory (the L2
-// cache holds it).  The activations are the A operand in shared memory in the
-// canonical K-major layout of umma.cuh; the accumulator uses up to 304 tensor-
-// memory columns.
+// Operands.  The A operands (x and the activations h1, h2, h3, as bf16 pairs)
+// live in tensor memory next to the accumulators: the epilogue reads an
+// accumulator row with tcgen05.ld and writes the activation row back with
+// tcgen05.st, and the next MMA reads A from tensor memory.  That leaves the
+// shared memory to the weights: W1, W3 and W4 stay resident (95 KB); W2
+// (185 KB, which does not fit beside them) is streamed every tile in K chunks
+// of 32 (19,456 bytes) through a 7-slot ring filled by bulk copies
+// (cp.async.bulk) from pre-laid-out copies in global memory (the L2 cache
+// holds them; CTAs read different replicas to spread the L2 traffic).
+//
+// Tensor-memory columns: accumulator 0..303, activations (A) 304..455,
+// layer-4 output 456..487, x (layer-1 A) 488..503.
 //
 // Roles in a CTA of 320 threads (one CTA per SM, persistent over a contiguous
 // range of tiles):
-//   warps 0-3  (WG0)  node work of the tile (pull, moments, x, final update,
-//                     store) and the epilogue of the low accumulator columns;
-//   warps 4-7  (WG1)  epilogue of the high accumulator columns;
+//   warps 0-3  (WG0)  the epilogue of the low accumulator columns, and the
+//                     final update and store of each tile (pull, moments,
+//                     conservation layer, BGK, force), done while the next
+//                     tile's second GEMM runs;
+//   warps 4-7  (WG1)  the epilogue of the high accumulator columns, and the
+//                     next tile's layer-1 operand (pull, moments, x), written
+//                     while the current tile's third GEMM runs;
 //   warp 8            MMA issue (one thread);
-//   warp 9            weight-ring producer (one thread).
+//   warp 9            W2 ring producer (one thread).
 // Hand-offs are mbarriers: x ready (128 arrivals), A ready (256 arrivals), the
-// accumulator ready (an MMA commit), and the ring's full/empty pairs.  Every
-// wait is bounded; on a time-out the kernel records it in shared memory, all
-// roles leave their loops, in-flight copies and MMAs are drained with bounded
-// waits, the tensor memory is freed and the timeout flag is set.
+// hidden accumulator ready and the output accumulator ready (MMA commits), and
+// the ring's full/empty pairs.  The layer-4 output and x have their own
+// tensor-memory columns, so the next tile's first GEMMs run while the output
+// is read.  Every wait is bounded; on a time-out the kernel records it in
+// shared memory, all roles leave their loops, in-flight copies and MMAs are
+// drained with bounded waits, the tensor memory is freed and the timeout flag
+// is set.
 #include <cuda_bf16.h>
 
 #include "d3q19.cuh"
@@ -53,20 +65,26 @@ constexpr int KH = 304;    // K of layers 2 and 3
 constexpr int N3 = 112;    // rows of W3
 constexpr int K4 = 112;    // K of layer 4
 constexpr int N4 = 32;     // rows of W4
-constexpr int KC = 32;     // K per streamed chunk
-constexpr int NCHUNK = 10; // 9 chunks of 32 + 1 of 16 per streamed matrix
-constexpr int SLOTS = 6;
+constexpr int KC = 32;     // K per streamed W2 chunk
+constexpr int NCHUNK = 10; // 9 chunks of 32 + 1 of 16
+constexpr int SLOTS = 7;
 constexpr int SLOT_BYTES = NH * KC * 2;  // 19,456
 constexpr int W1_BYTES = NH * KX * 2;    // 19,456
 constexpr int W4_BYTES = N4 * K4 * 2;    // 7,168
+constexpr int W3_BYTES = N3 * KH * 2;    // 68,096
 constexpr int W2_CHUNK = NH * KC * 2;    // 19,456 (the last chunk uses half)
-constexpr int W3_CHUNK = N3 * KC * 2;    // 7,168 (the last chunk uses half)
-// pre-laid-out weights in global memory (bytes)
+// one pre-laid-out copy of the weights in global memory (bytes)
 constexpr int G_W1 = 0;
 constexpr int G_W4 = G_W1 + W1_BYTES;
-constexpr int G_W2 = G_W4 + W4_BYTES;
-constexpr int G_W3 = G_W2 + NCHUNK * W2_CHUNK;
-constexpr int G_BYTES = G_W3 + NCHUNK * W3_CHUNK;  // 292,864
+constexpr int G_W3 = G_W4 + W4_BYTES;
+constexpr int G_W2 = G_W3 + W3_BYTES;
+constexpr int G_BYTES = G_W2 + NCHUNK * W2_CHUNK;  // 289,280 per copy
+// Every CTA streams the same 185 KB per tile; REPLICAS copies at different
+// addresses spread the reads over the L2 cache (CTA b reads copy b % REPLICAS).
+constexpr int REPLICAS = 8;
+
+// tensor-memory columns
+constexpr uint32_t TM_ACC = 0, TM_A = 304, TM_OUT = 456, TM_X = 488;
 
 constexpr int THREADS = 320;
 constexpr int MMA_WARP = 8, PROD_WARP = 9;
@@ -75,18 +93,19 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 struct __align__(1024) Smem {
   unsigned char w1[W1_BYTES];
   unsigned char w4[W4_BYTES];
-  unsigned char x[128 * KX * 2];
-  unsigned char a[128 * KH * 2];
+  unsigned char w3[W3_BYTES];
   unsigned char ring[SLOTS][SLOT_BYTES];
   unsigned long long full[SLOTS], empty[SLOTS];
-  unsigned long long xready, aready, accready, drain;
+  unsigned long long xready, aready, accready, outready, drain;
   uint32_t taddr;
   int err;
 };
 constexpr size_t SMEM_BYTES = sizeof(Smem) + 1024;
 static_assert(SMEM_BYTES <= 232448, "shared memory layout too large");
 
-__host__ __device__ constexpr int chunk_k(int c) { return c < NCHUNK - 1 ? KC : KH - KC * (NCHUNK - 1); }
+__host__ __device__ constexpr int chunk_k(int c) {
+  return c < NCHUNK - 1 ? KC : KH - KC * (NCHUNK - 1);
+}
 
 // ---- helpers ------------------------------------------------------------------
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -104,24 +123,52 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-// Bounded wait that also gives up early once another role has recorded an error.
+// Non-blocking test of a phase (mbarrier.test_wait never suspends the thread,
+// so a completed phase is seen at the next poll).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait that also gives up early once another role has recorded an
+// error.  Polls back off with a short sleep so that waiting warps leave the
+// issue slots to the warps that work.
 __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, volatile int *err) {
   for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && *err) return false;
+    if (mbar_test(bar, parity)) return true;
+    if ((it & 63u) == 63u && *err) return false;
+    __nanosleep(20);
   }
   atomicOr(const_cast<int *>(err), 1);
   return false;
 }
 // The same for a whole warp: lane 0 polls, the verdict is broadcast, so the
-// warp stays converged for the .sync.aligned tensor-memory loads that follow.
+// warp stays converged for the .sync.aligned tensor-memory accesses that follow.
 __device__ __forceinline__ bool wait_phase_warp(uint32_t bar, uint32_t parity, volatile int *err) {
   bool ok = true;
   if ((threadIdx.x & 31) == 0) ok = wait_phase(bar, parity, err);
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
-__device__ __forceinline__ void mma_ts(uint32_t d, uint64_t a, uint64_t b, uint32_t id, bool acc) {
-  mma_bf16(d, a, b, id, acc ? 1u : 0u);
+// D (+)= A[tmem] * B[smem]^T, one elected thread.
+__device__ __forceinline__ void mma_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t id,
+                                       bool acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(id), "r"(acc ? 1u : 0u)
+      : "memory");
+}
+// 8 consecutive columns of this thread's lane (the x8 form of tmem_st16).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
 }
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) { return pack_bf16x2(lo, hi); }
 __device__ __forceinline__ float lrelu(float v) { return fmaxf(v, LEAKY * v); }
@@ -153,28 +200,74 @@ __device__ __forceinline__ void pull19(const float *__restrict__ in, const Grid3
   }
 }
 
-// Drain accumulator columns [c0, c1) (multiples of 16) of this thread's row:
-// LeakyReLU, bf16, into K columns of the A operand row r (row length KH).
-// Columns at or above `kvalid` are not activations: `kvalid` gets the constant
-// 1 (the bias column) and the rest zero.
-__device__ __forceinline__ void drain_to_a(uint32_t tm_row, int c0, int c1, int kvalid,
-                                           unsigned char *a, int r) {
-  for (int c = c0; c < c1; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(tm_row + (uint32_t)c, v);
-    tmem_wait_ld();
-    float h[16];
+// Drain NCOL accumulator columns starting at C0 of this thread's row (loads
+// issued before one wait): LeakyReLU, bf16 pairs, into activation columns
+// TM_A + C0/2 of the same row.  Columns at or above KVALID are not
+// activations: KVALID gets the constant 1 (the bias column), the rest zero.
+template <int C0, int NCOL, int KVALID>
+__device__ __forceinline__ void drain_cols(uint32_t tm_row) {
+  static_assert(NCOL % 16 == 0 && NCOL <= 64, "16..64 columns per drain");
+  uint32_t v[NCOL];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int k = c + q;
-      h[q] = k < kvalid ? lrelu(__uint_as_float(v[q])) : (k == kvalid ? 1.0f : 0.0f);
+  for (int q = 0; q < NCOL / 16; ++q)
+    tmem_ld16(tm_row + (uint32_t)(TM_ACC + C0 + 16 * q),
+              *reinterpret_cast<uint32_t(*)[16]>(v + 16 * q));
+  tmem_wait_ld();
+  uint32_t p[NCOL / 2];
+#pragma unroll
+  for (int e = 0; e < NCOL / 2; ++e) {
+    float h[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k = C0 + 2 * e + j;
+      h[j] = k < KVALID ? lrelu(__uint_as_float(v[2 * e + j])) : (k == KVALID ? 1.0f : 0.0f);
     }
-    uint32_t p[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) p[q] = pack2(h[2 * q], h[2 * q + 1]);
-    *reinterpret_cast<uint4 *>(a + canon_offset(r, c, KH)) = make_uint4(p[0], p[1], p[2], p[3]);
-    *reinterpret_cast<uint4 *>(a + canon_offset(r, c + 8, KH)) = make_uint4(p[4], p[5], p[6], p[7]);
+    p[e] = pack2(h[0], h[1]);
   }
+#pragma unroll
+  for (int q = 0; q < NCOL / 32; ++q)
+    tmem_st16(tm_row + (uint32_t)(TM_A + C0 / 2 + 16 * q),
+              *reinterpret_cast<const uint32_t(*)[16]>(p + 16 * q));
+  if (NCOL % 32)
+    tmem_st8(tm_row + (uint32_t)(TM_A + C0 / 2 + 16 * (NCOL / 32)),
+             *reinterpret_cast<const uint32_t(*)[8]>(p + 16 * (NCOL / 32)));
+}
+
+// The low (WG0) or high (WG1) half of a 304-column accumulator -> h (K 0..303).
+__device__ __forceinline__ void drain_hidden(int wg, uint32_t tm_row) {
+  if (wg == 0) {
+    drain_cols<0, 64, H1>(tm_row);
+    drain_cols<64, 64, H1>(tm_row);
+    drain_cols<128, 32, H1>(tm_row);
+  } else {
+    drain_cols<160, 64, H1>(tm_row);
+    drain_cols<224, 64, H1>(tm_row);
+    drain_cols<288, 16, H1>(tm_row);
+  }
+}
+
+// x = (f - feq)/rho of this thread's node -> its row of the layer-1 operand
+// (19 inputs, the constant-1 bias column, zeros) in tensor memory.
+__device__ __forceinline__ void write_x(const float d[Q], bool active, uint32_t tm_row) {
+  const Moments m = node_moments(d);
+  float deq[Q];
+  shifted_feq(m, deq);
+  const float inv_rho = 1.0f / m.rho;
+  float xi[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    xi[i] = i < Q ? (active ? (d[i] - deq[i]) * inv_rho : 0.f) : (i == Q ? 1.0f : 0.0f);
+  uint32_t p[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) p[e] = pack2(xi[2 * e], xi[2 * e + 1]);
+  tmem_st16(tm_row + TM_X, p);
+}
+
+// Arrive on `bar` after this thread's tensor-memory stores are complete.
+__device__ __forceinline__ void publish(uint32_t bar) {
+  tmem_wait_st();
+  fence_before_sync();
+  mbar_arrive(bar);
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -185,15 +278,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                                       ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   volatile int *err = &S.err;
+  gw += (size_t)(blockIdx.x % REPLICAS) * G_BYTES;
 
   // ---- prologue: resident weights, barriers, tensor memory
   {
-    const uint4 *src1 = reinterpret_cast<const uint4 *>(gw + G_W1);
-    uint4 *dst1 = reinterpret_cast<uint4 *>(S.w1);
-    for (int e = tid; e < W1_BYTES / 16; e += THREADS) dst1[e] = src1[e];
-    const uint4 *src4 = reinterpret_cast<const uint4 *>(gw + G_W4);
-    uint4 *dst4 = reinterpret_cast<uint4 *>(S.w4);
-    for (int e = tid; e < W4_BYTES / 16; e += THREADS) dst4[e] = src4[e];
+    const uint4 *src = reinterpret_cast<const uint4 *>(gw + G_W1);
+    uint4 *dst = reinterpret_cast<uint4 *>(S.w1);
+    for (int e = tid; e < W1_BYTES / 16; e += THREADS) dst[e] = src[e];
+    src = reinterpret_cast<const uint4 *>(gw + G_W4);
+    dst = reinterpret_cast<uint4 *>(S.w4);
+    for (int e = tid; e < W4_BYTES / 16; e += THREADS) dst[e] = src[e];
+    src = reinterpret_cast<const uint4 *>(gw + G_W3);
+    dst = reinterpret_cast<uint4 *>(S.w3);
+    for (int e = tid; e < W3_BYTES / 16; e += THREADS) dst[e] = src[e];
   }
   if (tid == 0) {
     for (int s = 0; s < SLOTS; ++s) {
@@ -203,6 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     mbar_init(smem_u32(&S.xready), 128);
     mbar_init(smem_u32(&S.aready), 256);
     mbar_init(smem_u32(&S.accready), 1);
+    mbar_init(smem_u32(&S.outready), 1);
     mbar_init(smem_u32(&S.drain), 1);
     S.err = 0;
     fence_mbarrier_init();
@@ -219,240 +317,225 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   // ---- this CTA's contiguous range of tiles
   const int tiles_x = (g.nx + 127) / 128;
-  const long long ntiles_ll = (long long)tiles_x * g.ny * g.nz * g.batch;
-  const int ntiles = (int)ntiles_ll;
+  const int ntiles = (int)((long long)tiles_x * g.ny * g.nz * g.batch);
   const int per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
   const int t_begin = blockIdx.x * per + min((int)blockIdx.x, extra);
   const int count = per + ((int)blockIdx.x < extra ? 1 : 0);
 
   if (warp == PROD_WARP) {
-    // ---------------- weight-ring producer
+    // ---------------- W2 ring producer
     if (lane == 0) {
-      uint32_t uses[SLOTS] = {0, 0, 0, 0, 0, 0};
+      uint32_t used_mask = 0, par_mask = 0;  // per slot: used once; parity of its next use
       int slot = 0;
       bool ok = true;
       for (int t = 0; t < count && ok; ++t) {
-        for (int mat = 0; mat < 2 && ok; ++mat) {
-          for (int c = 0; c < NCHUNK; ++c) {
-            const uint32_t full = smem_u32(&S.full[slot]), empty = smem_u32(&S.empty[slot]);
-            if (uses[slot] > 0 && !wait_phase(empty, (uses[slot] - 1) & 1u, err)) {
-              ok = false;
-              break;
-            }
-            const int rows = mat == 0 ? NH : N3;
-            const uint32_t bytes = (uint32_t)(rows * chunk_k(c) * 2);
-            const unsigned char *src =
-                gw + (mat == 0 ? G_W2 + c * W2_CHUNK : G_W3 + c * W3_CHUNK);
-            mbar_arrive_expect_tx(full, bytes);
-            bulk_g2s(smem_u32(S.ring[slot]), src, bytes, full);
-            ++uses[slot];
-            slot = slot + 1 == SLOTS ? 0 : slot + 1;
+        for (int c = 0; c < NCHUNK; ++c) {
+          const uint32_t full = smem_u32(&S.full[slot]), empty = smem_u32(&S.empty[slot]);
+          const uint32_t bit = 1u << slot;
+          // the previous use of this slot must have been consumed
+          if ((used_mask & bit) && !wait_phase(empty, (par_mask & bit) ? 0u : 1u, err)) {
+            ok = false;
+            break;
           }
+          const uint32_t bytes = (uint32_t)(NH * chunk_k(c) * 2);
+          mbar_arrive_expect_tx(full, bytes);
+          bulk_g2s(smem_u32(S.ring[slot]), gw + G_W2 + c * W2_CHUNK, bytes, full);
+          used_mask |= bit;
+          par_mask ^= bit;
+          slot = slot + 1 == SLOTS ? 0 : slot + 1;
         }
       }
       // drain: every issued copy has landed before the CTA may exit
       for (int s = 0; s < SLOTS; ++s)
-        if (uses[s] > 0) {
+        if (used_mask & (1u << s)) {
           const uint32_t full = smem_u32(&S.full[s]);
+          const uint32_t last = (par_mask & (1u << s)) ? 0u : 1u;  // parity of the last use
           for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
-            if (mbar_try_wait(full, (uses[s] - 1) & 1u)) break;
+            if (mbar_test(full, last)) break;
         }
     }
   } else if (warp == MMA_WARP) {
     // ---------------- MMA issue
     if (lane == 0) {
-      const uint32_t sx = smem_u32(S.x), sa = smem_u32(S.a), sw1 = smem_u32(S.w1),
-                     sw4 = smem_u32(S.w4);
-      const uint32_t bar_acc = smem_u32(&S.accready);
+      const uint32_t sw1 = smem_u32(S.w1), sw3 = smem_u32(S.w3), sw4 = smem_u32(S.w4);
+      const uint32_t bar_acc = smem_u32(&S.accready), bar_out = smem_u32(&S.outready);
+      const uint32_t acc = tmem + TM_ACC, ah = tmem + TM_A, ax = tmem + TM_X;
       constexpr uint32_t ID160 = idesc_bf16_f32(128, 160), ID144 = idesc_bf16_f32(128, 144),
                          ID112 = idesc_bf16_f32(128, 112), ID32 = idesc_bf16_f32(128, 32);
-      uint32_t px = 0, pa = 0;
-      uint32_t uses[SLOTS] = {0, 0, 0, 0, 0, 0};
+      uint32_t px = 0, pa = 0, par_mask = 0;  // par bit s = parity of the slot's next use
       int slot = 0;
       bool issued = false;
       for (int t = 0; t < count; ++t) {
-        // L1: A = x (K 32), B = W1 resident
+        // L1: A = x (tensor memory, K 32), B = W1 resident
         if (!wait_phase(smem_u32(&S.xready), px, err)) break;
         px ^= 1;
         fence_after_sync();
 #pragma unroll
         for (int s = 0; s < KX / 16; ++s) {
-          const uint64_t a = smem_desc(sx + 256 * s, 128, 16 * KX);
-          mma_ts(tmem, a, smem_desc(sw1 + 256 * s, 128, 16 * KX), ID160, s > 0);
-          mma_ts(tmem + 160, a, smem_desc(sw1 + 20 * 16 * KX + 256 * s, 128, 16 * KX), ID144,
-                 s > 0);
+          mma_ta(acc, ax + 8 * s, smem_desc(sw1 + 256 * s, 128, 16 * KX), ID160, s > 0);
+          mma_ta(acc + 160, ax + 8 * s, smem_desc(sw1 + 20 * 16 * KX + 256 * s, 128, 16 * KX),
+                 ID144, s > 0);
         }
         mma_commit(bar_acc);
         issued = true;
-        // L2 and L3: A = activations (K 304), B = streamed chunks
+        // L2: A = h1 (tensor memory, K 304), B = streamed W2 chunks
+        if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
+        pa ^= 1;
+        fence_after_sync();
         bool ok = true;
-        for (int mat = 0; mat < 2 && ok; ++mat) {
-          if (!wait_phase(smem_u32(&S.aready), pa, err)) {
+        for (int c = 0; c < NCHUNK; ++c) {
+          const uint32_t bit = 1u << slot;
+          if (!wait_phase(smem_u32(&S.full[slot]), (par_mask & bit) ? 1u : 0u, err)) {
             ok = false;
             break;
           }
-          pa ^= 1;
+          par_mask ^= bit;
           fence_after_sync();
-          for (int c = 0; c < NCHUNK; ++c) {
-            if (!wait_phase(smem_u32(&S.full[slot]), uses[slot] & 1u, err)) {
-              ok = false;
-              break;
-            }
-            fence_after_sync();
-            const int kc = chunk_k(c);
-            const uint32_t sb = smem_u32(S.ring[slot]);
-            for (int s = 0; s < kc / 16; ++s) {
-              const uint64_t a = smem_desc(sa + 256 * (2 * c + s), 128, 16 * KH);
-              const bool acc = c > 0 || s > 0;
-              if (mat == 0) {
-                mma_ts(tmem, a, smem_desc(sb + 256 * s, 128, 16 * kc), ID160, acc);
-                mma_ts(tmem + 160, a, smem_desc(sb + 20 * 16 * kc + 256 * s, 128, 16 * kc),
-                       ID144, acc);
-              } else {
-                mma_ts(tmem, a, smem_desc(sb + 256 * s, 128, 16 * kc), ID112, acc);
-              }
-            }
-            mma_commit(smem_u32(&S.empty[slot]));
-            ++uses[slot];
-            slot = slot + 1 == SLOTS ? 0 : slot + 1;
+          const int kc = chunk_k(c);
+          const uint32_t sb = smem_u32(S.ring[slot]);
+          for (int s = 0; s < kc / 16; ++s) {
+            const uint32_t a = ah + 8 * (2 * c + s);
+            const bool accum = c > 0 || s > 0;
+            mma_ta(acc, a, smem_desc(sb + 256 * s, 128, 16 * kc), ID160, accum);
+            mma_ta(acc + 160, a, smem_desc(sb + 20 * 16 * kc + 256 * s, 128, 16 * kc), ID144,
+                   accum);
           }
-          if (ok) mma_commit(bar_acc);
+          mma_commit(smem_u32(&S.empty[slot]));
+          slot = slot + 1 == SLOTS ? 0 : slot + 1;
         }
         if (!ok) break;
-        // L4: A = h3 (K 112 of the activation rows), B = W4 resident
+        mma_commit(bar_acc);
+        // L3: A = h2, B = W3 resident (K 304, N 112)
+        if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
+        pa ^= 1;
+        fence_after_sync();
+#pragma unroll 1
+        for (int s = 0; s < KH / 16; ++s)
+          mma_ta(acc, ah + 8 * s, smem_desc(sw3 + 256 * s, 128, 16 * KH), ID112, s > 0);
+        mma_commit(bar_acc);
+        // L4: A = h3 (K 112), B = W4 resident; its own accumulator columns
         if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
         pa ^= 1;
         fence_after_sync();
 #pragma unroll
         for (int s = 0; s < K4 / 16; ++s)
-          mma_ts(tmem, smem_desc(sa + 256 * s, 128, 16 * KH),
-                 smem_desc(sw4 + 256 * s, 128, 16 * K4), ID32, s > 0);
-        mma_commit(bar_acc);
+          mma_ta(tmem + TM_OUT, ah + 8 * s, smem_desc(sw4 + 256 * s, 128, 16 * K4), ID32, s > 0);
+        mma_commit(bar_out);
       }
       // drain outstanding MMAs before the tensor memory is freed
       if (issued) {
         mma_commit(smem_u32(&S.drain));
         for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
-          if (mbar_try_wait(smem_u32(&S.drain), 0)) break;
+          if (mbar_test(smem_u32(&S.drain), 0)) break;
       }
     }
   } else {
     // ---------------- node and epilogue warpgroups
-    const int wg = warp >> 2;          // 0 or 1
-    const int r = tid & 127;           // tile row = tensor-memory lane
+    const int wg = warp >> 2;
+    const int r = tid & 127;
     const uint32_t tm_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    const uint32_t bar_acc = smem_u32(&S.accready), bar_a = smem_u32(&S.aready),
-                   bar_x = smem_u32(&S.xready);
-    uint32_t pacc = 0;
+    const uint32_t bar_acc = smem_u32(&S.accready), bar_out = smem_u32(&S.outready),
+                   bar_a = smem_u32(&S.aready), bar_x = smem_u32(&S.xready);
+    uint32_t pacc = 0, pout = 0;
+    const size_t vol = g.volume();
     Tile T;
     T.set(t_begin, tiles_x, g.ny, g.nz);
-    float d[Q];
+    Tile P = T;  // WG0: the tile whose final update is pending
+    float d[Q];  // WG0: populations of tile P; WG1: of the next tile to prepare
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = 0.f;
-    if (wg == 0 && count > 0 && T.x0 + r < g.nx) pull19(in, g, T, T.x0 + r, d);
-    const size_t vol = g.volume();
+    if (count > 0 && T.x0 + r < g.nx) pull19(in, g, T, T.x0 + r, d);
+    if (wg == 1 && count > 0) {
+      write_x(d, T.x0 + r < g.nx, tm_row);
+      publish(bar_x);
+    }
+
+    // WG0: final update of tile P from the layer-4 output; then load the
+    // populations of tile `next` (if any) for its own final update.
+    auto finish = [&](const Tile &next, bool have_next) -> bool {
+      const int x = P.x0 + r;
+      const bool active = x < g.nx;
+      const Moments m = node_moments(d);
+      {
+        const unsigned mask = __ballot_sync(0xffffffffu, active && is_unstable(m));
+        if (mask && lane == (__ffs(mask) - 1) && *reinterpret_cast<volatile int *>(flag) == 0)
+          atomicOr(flag, 1);
+      }
+      float deq[Q];
+      shifted_feq(m, deq);
+      if (!wait_phase_warp(bar_out, pout, err)) return false;
+      pout ^= 1;
+      fence_after_sync();
+      uint32_t v0[16], v1[16];
+      tmem_ld16(tm_row + TM_OUT, v0);
+      tmem_ld16(tm_row + TM_OUT + 16, v1);
+      tmem_wait_ld();
+      fence_before_sync();
+      float o[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(i < 16 ? v0[i] : v1[i - 16]);
+      project(o);
+      if (active) {
+        const float rw = m.rho * cp.omega;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = fmaf(cp.omega, deq[i] - d[i], d[i]) + rw * o[i];
+        const float Fx = cp.fx_y ? __ldg(cp.fx_y + P.y) : 0.f;
+        const float Fy = cp.fy_z ? __ldg(cp.fy_z + P.z) : 0.f;
+        const float Fz = cp.fz_x ? __ldg(cp.fz_x + x) : 0.f;
+        add_edm_force(m, Fx, Fy, Fz, d);
+        float *ob = out + (size_t)P.b * Q * vol + ((size_t)P.z * g.ny + P.y) * g.nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ob[(size_t)i * vol] = d[i];
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = 0.f;
+      if (have_next && next.x0 + r < g.nx) pull19(in, g, next, next.x0 + r, d);
+      P = next;
+      return true;
+    };
 
     for (int t = 0; t < count; ++t) {
-      const int x = T.x0 + r;
-      const bool active = x < g.nx;
-      Moments m = {0.f, 1.f, 0.f, 0.f, 0.f};
-      float deq[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) deq[i] = 0.f;
-      float inv_rho = 1.f;
-      if (wg == 0) {
-        // x = (f - feq)/rho -> row r of the layer-1 operand (19 + bias + zeros)
-        m = node_moments(d);
-        inv_rho = 1.0f / m.rho;
-        {
-          // sticky instability flag: one atomic at most per warp
-          const unsigned mask = __ballot_sync(0xffffffffu, active && is_unstable(m));
-          if (mask && lane == (__ffs(mask) - 1) && *reinterpret_cast<volatile int *>(flag) == 0)
-            atomicOr(flag, 1);
-        }
-        shifted_feq(m, deq);
-        float xi[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          xi[i] = i < Q ? (active ? (d[i] - deq[i]) * inv_rho : 0.f) : (i == Q ? 1.0f : 0.0f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4 *>(S.x + canon_offset(r, 8 * q, KX)) =
-              make_uint4(pack2(xi[8 * q], xi[8 * q + 1]), pack2(xi[8 * q + 2], xi[8 * q + 3]),
-                         pack2(xi[8 * q + 4], xi[8 * q + 5]), pack2(xi[8 * q + 6], xi[8 * q + 7]));
-        fence_proxy_async();
-        fence_before_sync();
-        mbar_arrive(bar_x);
-      }
-      // prefetch the next tile's populations while the GEMMs run
       Tile N = T;
-      float dn[Q];
+      const bool has_next = t + 1 < count;
+      if (has_next) N.set(t_begin + t + 1, tiles_x, g.ny, g.nz);
+      // L1 -> h1
+      if (!wait_phase_warp(bar_acc, pacc, err)) break;
+      pacc ^= 1;
+      fence_after_sync();
+      drain_hidden(wg, tm_row);
+      publish(bar_a);
+      if (wg == 0) {
+        if (t > 0 && !finish(T, true)) break;  // tile t-1 done; tile t's populations loaded
+      } else {
+        // the next tile's populations, needed after L2
 #pragma unroll
-      for (int i = 0; i < Q; ++i) dn[i] = 0.f;
-      if (wg == 0 && t + 1 < count) {
-        N.set(t_begin + t + 1, tiles_x, g.ny, g.nz);
-        if (N.x0 + r < g.nx) pull19(in, g, N, N.x0 + r, dn);
+        for (int i = 0; i < Q; ++i) d[i] = 0.f;
+        if (has_next && N.x0 + r < g.nx) pull19(in, g, N, N.x0 + r, d);
       }
-      // L1 -> h1, L2 -> h2 (N = 304: WG0 columns 0..159, WG1 160..303)
-      bool ok = true;
-      for (int layer = 0; layer < 2 && ok; ++layer) {
-        if (!wait_phase_warp(bar_acc, pacc, err)) {
-          ok = false;
-          break;
-        }
-        pacc ^= 1;
-        fence_after_sync();
-        if (wg == 0)
-          drain_to_a(tm_row, 0, 160, 300, S.a, r);
-        else
-          drain_to_a(tm_row, 160, 304, 300, S.a, r);
-        fence_proxy_async();
-        fence_before_sync();
-        mbar_arrive(bar_a);
+      // L2 -> h2
+      if (!wait_phase_warp(bar_acc, pacc, err)) break;
+      pacc ^= 1;
+      fence_after_sync();
+      drain_hidden(wg, tm_row);
+      publish(bar_a);
+      if (wg == 1 && has_next) {
+        // the next tile's layer-1 operand (L1 of this tile has read x)
+        write_x(d, N.x0 + r < g.nx, tm_row);
+        publish(bar_x);
       }
-      if (!ok) break;
-      // L3 -> h3 (N = 112: WG0 columns 0..63, WG1 64..111; K columns 100.. = 1, 0, ...)
+      // L3 -> h3 (K 0..99, the constant column at 100, zeros to 111)
       if (!wait_phase_warp(bar_acc, pacc, err)) break;
       pacc ^= 1;
       fence_after_sync();
       if (wg == 0)
-        drain_to_a(tm_row, 0, 64, 100, S.a, r);
+        drain_cols<0, 64, H3>(tm_row);
       else
-        drain_to_a(tm_row, 64, 112, 100, S.a, r);
-      fence_proxy_async();
-      fence_before_sync();
-      mbar_arrive(bar_a);
-      // L4 -> o, conservation layer, BGK + correction + force, store (WG0)
-      if (!wait_phase_warp(bar_acc, pacc, err)) break;
-      pacc ^= 1;
-      fence_after_sync();
-      if (wg == 0) {
-        uint32_t v0[16], v1[16];
-        tmem_ld16(tm_row, v0);
-        tmem_ld16(tm_row + 16, v1);
-        tmem_wait_ld();
-        float o[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(i < 16 ? v0[i] : v1[i - 16]);
-        project(o);
-        if (active) {
-          const float rw = m.rho * cp.omega;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) d[i] = fmaf(cp.omega, deq[i] - d[i], d[i]) + rw * o[i];
-          const float Fx = cp.fx_y ? __ldg(cp.fx_y + T.y) : 0.f;
-          const float Fy = cp.fy_z ? __ldg(cp.fy_z + T.z) : 0.f;
-          const float Fz = cp.fz_x ? __ldg(cp.fz_x + x) : 0.f;
-          add_edm_force(m, Fx, Fy, Fz, d);
-          float *ob = out + (size_t)T.b * Q * vol + ((size_t)T.z * g.ny + T.y) * g.nx + x;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) ob[(size_t)i * vol] = d[i];
-        }
-        fence_before_sync();
-      }
-#pragma unroll
-      for (int i = 0; i < Q; ++i) d[i] = dn[i];
+        drain_cols<64, 48, H3>(tm_row);
+      publish(bar_a);
       T = N;
     }
+    // WG0: the last tile's final update
+    if (wg == 0 && count > 0 && !*err) finish(T, false);
   }
 
   // ---- teardown: every role has left its loop (normally or on an error)
@@ -463,10 +546,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (tid == 0 && S.err) atomicOr(timeout_flag, 1);
 }
 
-// FP32 packed weights -> BF16 operand tiles in the canonical K-major layout,
-// each streamed chunk contiguous, biases in the constant-1 K column.
+// FP32 packed weights -> BF16 operand tiles in the canonical K-major layout
+// (W1, W3, W4 whole; W2 as contiguous K chunks), biases in the constant-1 K
+// column, REPLICAS copies.
 __global__ void k3_prepare_weights(Mlp3 w, unsigned char *__restrict__ gw) {
-  const int total = NH * KX + N4 * K4 + NH * KH + N3 * KH;
+  const int total = NH * KX + N4 * K4 + N3 * KH + NH * KH;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     float v = 0.f;
     size_t off;
@@ -478,24 +562,25 @@ __global__ void k3_prepare_weights(Mlp3 w, unsigned char *__restrict__ gw) {
       const int f = e - NH * KX, n = f / K4, k = f % K4;
       if (n < Q) v = k < H3 ? w.w4[n * H3 + k] : (k == H3 ? w.b4[n] : 0.f);
       off = G_W4 + canon_offset(n, k, K4);
-    } else if (e < NH * KX + N4 * K4 + NH * KH) {  // W2 chunks
+    } else if (e < NH * KX + N4 * K4 + N3 * KH) {  // W3: rows n < 100, K 300, bias at 300
       const int f = e - NH * KX - N4 * K4, n = f / KH, k = f % KH;
+      if (n < H3) v = k < H2 ? w.w3[n * H2 + k] : (k == H2 ? w.b3[n] : 0.f);
+      off = G_W3 + canon_offset(n, k, KH);
+    } else {  // W2 chunks
+      const int f = e - NH * KX - N4 * K4 - N3 * KH, n = f / KH, k = f % KH;
       if (n < H2) v = k < H1 ? w.w2[n * H1 + k] : (k == H1 ? w.b2[n] : 0.f);
       const int c = k / KC;
       off = G_W2 + (size_t)c * W2_CHUNK + canon_offset(n, k % KC, chunk_k(c));
-    } else {  // W3 chunks
-      const int f = e - NH * KX - N4 * K4 - NH * KH, n = f / KH, k = f % KH;
-      if (n < H3) v = k < H2 ? w.w3[n * H2 + k] : (k == H2 ? w.b3[n] : 0.f);
-      const int c = k / KC;
-      off = G_W3 + (size_t)c * W3_CHUNK + canon_offset(n, k % KC, chunk_k(c));
     }
-    *reinterpret_cast<__nv_bfloat16 *>(gw + off) = __float2bfloat16_rn(v);
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    for (int rep = 0; rep < REPLICAS; ++rep)
+      *reinterpret_cast<__nv_bfloat16 *>(gw + (size_t)rep * G_BYTES + off) = b;
   }
 }
 
 }  // namespace
 
-size_t mlp_tc_weight_bytes() { return (size_t)G_BYTES; }
+size_t mlp_tc_weight_bytes() { return (size_t)G_BYTES * REPLICAS; }
 
 cudaError_t launch_prepare_weights_tc(const Mlp3 &w, void *gw, cudaStream_t s) {
   k3_prepare_weights<<<256, 256, 0, s>>>(w, static_cast<unsigned char *>(gw));
