@@ -365,10 +365,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t px = 0, pa = 0, par_mask = 0;  // par bit s = parity of the slot's next use
       int slot = 0;
       bool issued = false;
-      for (int t = 0; t < count; ++t) {
+      // the first tile's x (later tiles' x is awaited after the L4 commit)
+      bool xok = count > 0 && wait_phase(smem_u32(&S.xready), px, err);
+      px ^= 1;
+      for (int t = 0; t < count && xok; ++t) {
         // L1: A = x (tensor memory, K 32), B = W1 resident
-        if (!wait_phase(smem_u32(&S.xready), px, err)) break;
-        px ^= 1;
         fence_after_sync();
 #pragma unroll
         for (int s = 0; s < KX / 16; ++s) {
@@ -378,19 +379,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mma_commit(bar_acc);
         issued = true;
-        // L2: A = h1 (tensor memory, K 304), B = streamed W2 chunks
+        // L2: A = h1 (tensor memory, K 304), B = streamed W2 chunks, consumed
+        // as they land (the stream from the L2 cache sets the pace).  Note that
+        // on this GPU the first memory access of a thread after a
+        // tcgen05.commit waits until the MMAs it has issued have completed.
         if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
         pa ^= 1;
         fence_after_sync();
         bool ok = true;
         for (int c = 0; c < NCHUNK; ++c) {
-          const uint32_t bit = 1u << slot;
-          if (!wait_phase(smem_u32(&S.full[slot]), (par_mask & bit) ? 1u : 0u, err)) {
+          if (!wait_phase(smem_u32(&S.full[slot]), (par_mask >> slot) & 1u, err)) {
             ok = false;
             break;
           }
-          par_mask ^= bit;
-          fence_after_sync();
+          par_mask ^= 1u << slot;
           const int kc = chunk_k(c);
           const uint32_t sb = smem_u32(S.ring[slot]);
           for (int s = 0; s < kc / 16; ++s) {
@@ -421,6 +423,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int s = 0; s < K4 / 16; ++s)
           mma_ta(tmem + TM_OUT, ah + 8 * s, smem_desc(sw4 + 256 * s, 128, 16 * K4), ID32, s > 0);
         mma_commit(bar_out);
+        if (t + 1 < count) {  // the next tile's x
+          xok = wait_phase(smem_u32(&S.xready), px, err);
+          px ^= 1;
+        }
       }
       // drain outstanding MMAs before the tensor memory is freed
       if (issued) {
