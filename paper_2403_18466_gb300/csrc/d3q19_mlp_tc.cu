@@ -138,11 +138,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 // Bounded wait that also gives up early once another role has recorded an
 // error.  Polls back off with a short sleep so that waiting warps leave the
 // issue slots to the warps that work.
+template <bool SLEEP = true>
 __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, volatile int *err) {
   for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
     if (mbar_test(bar, parity)) return true;
     if ((it & 63u) == 63u && *err) return false;
-    __nanosleep(20);
+    if (SLEEP) __nanosleep(20);
   }
   atomicOr(const_cast<int *>(err), 1);
   return false;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int slot = 0;
       bool issued = false;
       // the first tile's x (later tiles' x is awaited after the L4 commit)
-      bool xok = count > 0 && wait_phase(smem_u32(&S.xready), px, err);
+      bool xok = count > 0 && wait_phase<false>(smem_u32(&S.xready), px, err);
       px ^= 1;
       for (int t = 0; t < count && xok; ++t) {
         // L1: A = x (tensor memory, K 32), B = W1 resident
@@ -383,12 +384,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         // as they land (the stream from the L2 cache sets the pace).  Note that
         // on this GPU the first memory access of a thread after a
         // tcgen05.commit waits until the MMAs it has issued have completed.
-        if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
+        if (!wait_phase<false>(smem_u32(&S.aready), pa, err)) break;
         pa ^= 1;
         fence_after_sync();
         bool ok = true;
         for (int c = 0; c < NCHUNK; ++c) {
-          if (!wait_phase(smem_u32(&S.full[slot]), (par_mask >> slot) & 1u, err)) {
+          if (!wait_phase<false>(smem_u32(&S.full[slot]), (par_mask >> slot) & 1u, err)) {
             ok = false;
             break;
           }
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!ok) break;
         mma_commit(bar_acc);
         // L3: A = h2, B = W3 resident (K 304, N 112)
-        if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
+        if (!wait_phase<false>(smem_u32(&S.aready), pa, err)) break;
         pa ^= 1;
         fence_after_sync();
 #pragma unroll 1
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mma_ta(acc, ah + 8 * s, smem_desc(sw3 + 256 * s, 128, 16 * KH), ID112, s > 0);
         mma_commit(bar_acc);
         // L4: A = h3 (K 112), B = W4 resident; its own accumulator columns
-        if (!wait_phase(smem_u32(&S.aready), pa, err)) break;
+        if (!wait_phase<false>(smem_u32(&S.aready), pa, err)) break;
         pa ^= 1;
         fence_after_sync();
 #pragma unroll
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mma_ta(tmem + TM_OUT, ah + 8 * s, smem_desc(sw4 + 256 * s, 128, 16 * K4), ID32, s > 0);
         mma_commit(bar_out);
         if (t + 1 < count) {  // the next tile's x
-          xok = wait_phase(smem_u32(&S.xready), px, err);
+          xok = wait_phase<false>(smem_u32(&S.xready), px, err);
           px ^= 1;
         }
       }
