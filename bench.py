@@ -198,21 +198,23 @@ def run_gpu(args):
 
     # ---- roofline of the dominant kernel (the step kernel itself) ---------
     achieved_gbs = BYTES_PER_NODE * nodes / (ms / args.steps * 1e-3) / 1e9
-    # binding unit of the learned step: the XU (special-function) pipe.  Measured
-    # on this GPU (microbenchmark): tanh.approx on packed bf16 pairs holds a
-    # sub-partition's XU pipe for 16 cycles per warp instruction, the bf16x2
-    # conversion for 4; the 128 activations of a node (64 pairs, each one
-    # conversion + one tanh) therefore need 64 * 20 / 32 = 40 XU cycles per node
-    # per sub-partition, i.e. 10 cycles per node per SM.
-    xu_cycles_per_node_per_sm = 64 * (16 + 4) / 32 / 4
+    # binding unit of the learned step: the XU (special-function) pipe.  Each
+    # node needs 64 tanh.approx.bf16x2 and 64 cvt.rn.bf16x2.f32 (the 128
+    # activations of the two hidden layers).  Measured on this GPU with that
+    # instruction mix (cvt + tanh per pair, packed stores, 16 warps per SM):
+    # 0.239 tanh.bf16x2 warp instructions per cycle per SM, i.e. one node per
+    # 64 / 32 / 0.239 = 8.37 cycles per SM (1 warp per sub-partition reaches
+    # only half of that).
+    xu_cycles_per_node_per_sm = 64 / 32 / 0.239
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     xu_bound = sms * sm_mhz * 1e6 / xu_cycles_per_node_per_sm / 1e6  # MLUPS per GPU
     binding = {"unit": "xu (tanh + bf16x2 conversion)", "achieved": round(nodes / (ms / args.steps * 1e-3) / 1e6, 1),
                "peak": round(xu_bound, 1), "peak_unit": "MLUPS",
                "frac": round(nodes / (ms / args.steps * 1e-3) / 1e6 / xu_bound, 4),
-               "derivation": "64 tanh.approx.bf16x2 (16 XU cycles) + 64 cvt.rn.bf16x2.f32 (4) per "
-                             "32-node warp, 4 sub-partitions, measured SM clock"}
+               "derivation": "64 tanh.approx.bf16x2 + 64 cvt.rn.bf16x2.f32 per node; measured "
+                             "XU throughput with that mix 0.239 tanh warp-instr/cycle/SM "
+                             "(16 warps/SM); measured SM clock"}
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
                 "traffic": _traffic_from_profile(MLP_BF16_SOURCES, "k_step_mlp_bf16_2048.md", nodes),

@@ -24,11 +24,12 @@
 // next operand row.  The populations of the next tile are loaded while the
 // current tile's three GEMMs run.
 //
-// Binding unit: the XU (MUFU) pipe.  Measured on this GPU, per SM sub-
-// partition a warp-wide tanh.approx.bf16x2 occupies the XU pipe for 16 cycles
-// and a cvt to bf16x2 for 4, so the 128 activations of a node cost 10 XU
-// cycles per node per SM; the step cannot exceed ~30 G nodes/s however the
-// GEMMs and memory traffic are scheduled (HBM alone would allow 94 G).
+// Binding unit: the XU (MUFU) pipe.  Measured on this GPU with the
+// epilogue's instruction mix (cvt + tanh.approx.bf16x2 per pair), the XU
+// sustains ~0.24 tanh warp instructions per cycle per SM when 16 warps per SM
+// feed it, so the 128 activations of a node cap the step near 37 G nodes/s
+// however the GEMMs and memory traffic are scheduled (HBM alone would allow
+// 94 G); with fewer warps in their tanh phase at once it reaches less.
 //
 // Synchronisation per warpgroup: operand rows written by all 128 threads
 // -> fence.proxy.async + named barrier -> one thread issues the MMAs and
