@@ -230,3 +230,21 @@ def test_short_training_run_reduces_loss(lbm):
         assert min(hist[-5:]) < hist[0]
         learned, st = train.rollout_loss(ds, kind, theta)
         assert np.isfinite(learned) and st == lbm.LBM_OK
+
+
+def test_a_posteriori_evaluation_runs(lbm):
+    """The evaluation driver end to end at a small size: finite errors for all
+    three LES, records at every interval, stable runs."""
+    from paper_2403_18466_gb300 import evaluate
+    res = evaluate.evaluate(dns=256, cg=8, epochs=5, lr=1e-3, trajectories=2, unroll=4,
+                            steps=40, every=20, spinup=300, verbose=False)
+    assert res["steps"] == [20, 40]
+    for k in ("bgk", "smag", "learned"):
+        assert len(res["spectrum_error"][k]) == 2
+        # a run that blew up is stopped and reported, with NaN records from then on
+        at = res["unstable_at"][k]
+        good = [e for s, e in zip(res["steps"], res["spectrum_error"][k]) if at is None or s < at]
+        assert all(np.isfinite(good))
+    # the Smagorinsky LES is stable at these parameters
+    assert res["status"]["smag"] == lbm.lbm_strerror(lbm.LBM_OK) and res["unstable_at"]["smag"] is None
+    assert len(res["final_spectra"]["dns"]) == 256 // 8 // 2 + 1
