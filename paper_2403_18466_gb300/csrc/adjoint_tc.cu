@@ -8,18 +8,31 @@
 //   lam_i(x - c_i) = [J_C(f(x))^T lam'(x)]_i,   dtheta += sum_x (dC/dtheta)^T lam'(x).
 //
 // A warpgroup owns a 128-node tile (thread r = node r = TMEM lane r) and runs
-// nine GEMMs with M = 128 nodes:
+// six GEMMs with M = 128 nodes:
 //   forward recompute   x|1 . W1'^T -> tanh -> h1|1 . W2'^T -> tanh -> h2|1 . W3'^T = o
 //   backward            dL/do . W3 -> *(1-h2^2) = dL/da2 ;  dL/da2 . W2 -> *(1-h1^2) = dL/da1 ;
 //                       dL/da1 . W1 = dL/dx
-// and then three weight-gradient GEMMs with the NODES as the reduction
-// dimension (K = 128), M = 64 hidden units, reading the same node-row operand
-// buffers as MN-major matrices, accumulated in tensor memory over all of the
-// warpgroup's tiles:
-//   [dW2 | db2] += dL/da2^T . [h1 | 1],  [dW1 | db1] += dL/da1^T . [x | 1],
-//   dW3^T += h2^T . dL/do                 (db3 = sum dL/do on the CUDA cores)
-// Each warpgroup finally adds its sums to its own row of partial sums, which a
-// fixed-order reduction turns into dtheta (bitwise reproducible).
+// The weight gradients are three GEMMs with the NODES as the reduction
+// dimension (K = 16 nodes per MMA), M = 64 hidden units, reading the same
+// node-row operand buffers as MN-major matrices:
+//   dW3^T += h2^T . dL/do,  [dW2 | db2] += dL/da2^T . [h1 | 1],  [dW1 | db1] += dL/da1^T . [x | 1]
+// (db3 = sum dL/do on the CUDA cores).
+//
+// Organisation (one persistent CTA per SM): three warpgroups, each with one
+// tile in flight and its own 128 tensor-memory columns (accumulator and the
+// two tanh derivatives), plus three issuer warps, one per weight-gradient
+// GEMM (dW3, dW2, dW1), each accumulating the whole CTA's sum of its matrix
+// (112 columns in all).  A warpgroup signals the issuer concerned as soon as
+// the operands of that GEMM are complete (dL/do, then dL/da2, then dL/da1) and
+// carries on with its own chain; it waits for an issuer only before it
+// overwrites a buffer that issuer's GEMM reads.  An issuer takes the
+// warpgroups' GEMMs in a fixed order (tile, then warpgroup), so every sum is
+// accumulated in the same order on every run; an issuer thread stalls until
+// its GEMM has completed before it can poll again, which is why the three
+// matrices have an issuer each.  dL/da1 reuses the h2 buffer once the dW3 GEMM
+// has read it.
+// Every wait is bounded: on a time-out all roles leave their loops, the
+// tensor memory is freed and the timeout flag is set.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -32,22 +45,26 @@ namespace {
 using namespace umma;
 
 constexpr int WG_THREADS = 128;
-constexpr int WGS = 2;
-constexpr int THREADS = WGS * WG_THREADS;
+constexpr int WGS = 3;                  // tile warpgroups per CTA
+constexpr int DW_WARP = WGS * 4;        // warp index of the first weight-gradient issuer
+constexpr int THREADS = WGS * WG_THREADS + 3 * 32;
 constexpr int K1 = 16, K2 = 80;
-constexpr uint32_t TMEM_COLS = 512;  // 256 per warpgroup
-// per-warpgroup column offsets: GEMM accumulator, the weight-gradient sums,
-// and the tanh derivatives 1 - h^2 of both hidden layers (bf16 pairs)
-constexpr uint32_t C_D = 0, C_DW2 = 64, C_DW1 = 144, C_DW3 = 160, C_DH1 = 176, C_DH2 = 208;
+constexpr uint32_t TMEM_COLS = 512;
+// per-warpgroup block: GEMM accumulator, tanh derivatives 1 - h^2 of both
+// hidden layers (bf16 pairs)
+constexpr uint32_t C_D = 0, C_DH1 = 64, C_DH2 = 96, WG_COLS = 128;
+// weight-gradient sums of the CTA (M = 64 accumulators)
+constexpr uint32_t C_DW2 = WGS * WG_COLS, C_DW1 = C_DW2 + 80, C_DW3 = C_DW1 + 16;
+static_assert(C_DW3 + 16 <= TMEM_COLS, "tensor memory layout");
 constexpr uint32_t WAIT_LIMIT = 1u << 20;
+enum { ST_DW3 = 0, ST_DW2 = 1, ST_DW1 = 2, STAGES = 3 };
 
 struct __align__(16) WgBuffers {
   unsigned char a1[128 * K1 * 2];   // x | 1 | 0        (node rows)
   unsigned char h1[128 * K2 * 2];   // h1 | 1 | 0
-  unsigned char h2[128 * K2 * 2];   // h2 | 1 | 0
+  unsigned char h2[128 * K2 * 2];   // h2 | 1 | 0, then dL/da1 (row length 64)
   unsigned char ob[128 * 16 * 2];   // dL/do | 0
   unsigned char a2b[128 * 64 * 2];  // dL/da2
-  unsigned char a1b[128 * 64 * 2];  // dL/da1
 };
 
 struct __align__(1024) Smem {
@@ -58,9 +75,13 @@ struct __align__(1024) Smem {
   unsigned char w2t[HIDDEN * 64 * 2]; // [64 x 64]  [k][j] = W2[j][k]
   unsigned char w1t[16 * 64 * 2];     // [16 x 64]  [i][j] = W1[j][i]
   WgBuffers wb[WGS];
-  unsigned long long bar[WGS];
-  float db3[WGS][4][9];
+  unsigned long long bar[WGS];          // the warpgroup's own GEMMs (commit)
+  unsigned long long rdy[WGS][STAGES];  // operands of a weight-gradient GEMM written
+  unsigned long long dwd[WGS][STAGES];  // that GEMM has completed (commit)
+  unsigned long long drain[STAGES];
+  float db3[WGS * 4][9];
   uint32_t taddr;
+  int err;
 };
 constexpr size_t SMEM_BYTES = sizeof(Smem) + 1024;
 static_assert(SMEM_BYTES <= 227 * 1024, "adjoint shared memory too large");
@@ -95,6 +116,20 @@ __device__ __forceinline__ void feq_partials(float rho, float ux, float uy, int 
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
+// tanh(a) and 1 - tanh(a)^2 from t = e^{-2|a|} and r = 1/(1 + t): with
+// u = t r, tanh a = sign(a) (r - u) and 1 - tanh^2 a = 4 u r.  Two XU
+// operations (ex2, rcp); the derivative keeps its relative accuracy for
+// saturated units, where 1 - h^2 formed from an approximate h would not.
+__device__ __forceinline__ void tanh_and_slope(float a, float &h, float &dh) {
+  float t, r;
+  const float e = -2.8853900817779268f * fabsf(a);  // -2 log2(e) |a|
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(e));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
+  const float u = t * r;
+  h = copysignf(r - u, a);
+  dh = 4.0f * (u * r);
+}
+
 // D (64 FP32 columns of this thread's row) -> h = tanh(D) in FP32 -> bf16 row of
 // `dst` (K columns 0..63, the next GEMM's operand), and the derivative 1 - h^2,
 // computed to a few ulp in FP32 and rounded to bf16 pairs, into 32 TMEM
@@ -111,10 +146,10 @@ __device__ __forceinline__ void tanh_row(uint32_t tm_row, unsigned char *dst, in
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       float h0, h1, d0, d1;
-      tanh_and_derivative(__uint_as_float(v[2 * e]), h0, d0);
-      tanh_and_derivative(__uint_as_float(v[2 * e + 1]), h1, d1);
-      p[e] = pack_bf16x2_alu(h0, h1);
-      q[e] = pack_bf16x2_alu(d0, d1);
+      tanh_and_slope(__uint_as_float(v[2 * e]), h0, d0);
+      tanh_and_slope(__uint_as_float(v[2 * e + 1]), h1, d1);
+      p[e] = pack_bf16x2(h0, h1);
+      q[e] = pack_bf16x2(d0, d1);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
@@ -161,6 +196,34 @@ struct TilePos {
   }
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait of one thread; gives up early once another role has recorded
+// an error, and records one itself on a time-out.
+__device__ __forceinline__ bool wait_flag(uint32_t bar, uint32_t parity, volatile int *err) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 15u) == 15u && *err) return false;
+  }
+  atomicOr(const_cast<int *>(err), 1);
+  return false;
+}
+// Warpgroup-wide wait on one or two barriers: the leader polls, the named
+// barrier hands every thread the same verdict.
+__device__ __forceinline__ bool wg_wait(uint32_t b0, uint32_t p0, uint32_t b1, uint32_t p1,
+                                        bool two, bool leader, uint32_t bar_id,
+                                        volatile int *err) {
+  bool fail = false;
+  if (leader) {
+    fail = !wait_flag(b0, p0, err);
+    if (!fail && two) fail = !wait_flag(b1, p1, err);
+  }
+  const bool any = barrier_any(bar_id, WG_THREADS, fail);
+  fence_after_sync();
+  return !any;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_adjoint_tc(const float *__restrict__ state, const float *__restrict__ lam_next,
                  float *__restrict__ lam_out, int nx, int ny, int batch, CollideParams p,
@@ -168,10 +231,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                       ~uintptr_t(1023));
-  const int tid = threadIdx.x;
-  const int wg = tid / WG_THREADS;
-  const int r = tid % WG_THREADS;
-  const int warp_in_wg = r / 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int *err = &S.err;
 
   // ---- prologue: weights in the six operand layouts
   for (int e = tid; e < HIDDEN * K1; e += THREADS) {
@@ -200,17 +261,28 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int i = e / HIDDEN, j = e % HIDDEN;
     store_bf16(S.w1t, i, j, 64, i < 9 ? w.w1[j * 9 + i] : 0.f);
   }
-  WgBuffers &B = S.wb[wg];
-  // constant columns 64..79 of the h1 / h2 rows: 1, 0, ..., 0
-  for (unsigned char *hb : {B.h1, B.h2}) {
-    *reinterpret_cast<uint4 *>(hb + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(hb + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
+  if (warp < DW_WARP) {
+    // constant columns 64..79 of the h1 / h2 rows: 1, 0, ..., 0
+    WgBuffers &B = S.wb[warp >> 2];
+    const int r = tid & 127;
+    for (unsigned char *hb : {B.h1, B.h2}) {
+      *reinterpret_cast<uint4 *>(hb + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(hb + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   if (tid == 0) {
-    for (int k = 0; k < WGS; ++k) mbar_init(smem_u32(&S.bar[k]), 1);
+    for (int g = 0; g < WGS; ++g) {
+      mbar_init(smem_u32(&S.bar[g]), 1);
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(smem_u32(&S.rdy[g][s]), 1);
+        mbar_init(smem_u32(&S.dwd[g][s]), 1);
+      }
+    }
+    for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&S.drain[s]), 1);
+    S.err = 0;
     fence_mbarrier_init();
   }
-  if (tid < 32) {
+  if (warp == 0) {
     tmem_alloc(smem_u32(&S.taddr), TMEM_COLS);
     tmem_relinquish();
   }
@@ -218,303 +290,384 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-
-  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 256);
-  const uint32_t lane_off = (uint32_t)(32 * warp_in_wg) << 16;
-  const uint32_t tm_row = tm_wg + C_D + lane_off;
-  const uint32_t bar = smem_u32(&S.bar[wg]);
-  const uint32_t bar_id = 1 + wg;
-  const bool leader = r == 0;
-  const uint32_t s_a1 = smem_u32(B.a1), s_h1 = smem_u32(B.h1), s_h2 = smem_u32(B.h2);
-  const uint32_t s_ob = smem_u32(B.ob), s_a2b = smem_u32(B.a2b), s_a1b = smem_u32(B.a1b);
-  const uint32_t s_w1 = smem_u32(S.w1), s_w2 = smem_u32(S.w2), s_w3 = smem_u32(S.w3);
-  const uint32_t s_w3t = smem_u32(S.w3t), s_w2t = smem_u32(S.w2t), s_w1t = smem_u32(S.w1t);
-  constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
-  // weight-gradient GEMMs: M = 64, both operands MN-major (bits 15, 16)
-  constexpr uint32_t IDW80 = idesc_bf16_f32(64, 80) | (1u << 15) | (1u << 16);
-  constexpr uint32_t IDW16 = idesc_bf16_f32(64, 16) | (1u << 15) | (1u << 16);
+  const uint32_t tmem = S.taddr;
 
   const int plane = nx * ny;
   const int tiles_x = (nx + WG_THREADS - 1) / WG_THREADS;
   const int ntiles = tiles_x * ny * batch;
   const int nwg = gridDim.x * WGS;
-  const int gwg = blockIdx.x * WGS + wg;
-  const int per = ntiles / nwg, extra = ntiles % nwg;
-  const int t_begin = gwg * per + min(gwg, extra);
-  const int count = per + (gwg < extra ? 1 : 0);
-  TilePos T;
-  T.x0 = (t_begin % tiles_x) * WG_THREADS;
-  T.y = (t_begin / tiles_x) % ny;
-  T.b = t_begin / (tiles_x * ny);
-  const float omega = p.omega;
-
-  uint32_t phase = 0;
-  bool fail = false;
+  auto range = [&](int g, int &begin, int &count) {
+    const int gwg = blockIdx.x * WGS + g;
+    const int per = ntiles / nwg, extra = ntiles % nwg;
+    begin = gwg * per + min(gwg, extra);
+    count = per + (gwg < extra ? 1 : 0);
+  };
+  // weight-gradient GEMMs: M = 64, both operands MN-major (bits 15, 16)
+  constexpr uint32_t IDW80 = idesc_bf16_f32(64, 80) | (1u << 15) | (1u << 16);
+  constexpr uint32_t IDW16 = idesc_bf16_f32(64, 16) | (1u << 15) | (1u << 16);
   float db3[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) db3[i] = 0.f;
+  bool any_tiles = false;
 
-// leader waits for the warpgroup's last commit; the named barrier carries the verdict
-#define WAIT_OR_BREAK()                                                  \
-  if (leader) fail = !mbar_wait_bounded(bar, phase, WAIT_LIMIT);         \
-  if (barrier_any(bar_id, WG_THREADS, fail)) break;                      \
-  phase ^= 1;                                                            \
-  fence_after_sync();
-// all operand rows written: make them visible to the tensor core, then one thread issues
-#define OPERANDS_READY()               \
-  fence_proxy_async();                 \
-  fence_before_sync();                 \
+  if (warp >= DW_WARP) {
+    // ---------------- weight-gradient issuers: warp DW_WARP + s runs stage s
+    const int s = warp - DW_WARP;
+    if (lane == 0) {
+      int cnt[WGS];
+      int rounds = 0;
+#pragma unroll
+      for (int g = 0; g < WGS; ++g) {
+        int b;
+        range(g, b, cnt[g]);
+        rounds = max(rounds, cnt[g]);
+      }
+      uint32_t par = 0;  // bit g: parity of rdy[g][s]
+      bool started = false, ok = true;
+      const uint32_t acc_col = s == ST_DW3 ? C_DW3 : (s == ST_DW2 ? C_DW2 : C_DW1);
+      const uint32_t id = s == ST_DW2 ? IDW80 : IDW16;
+      for (int k = 0; k < rounds && ok; ++k) {
+#pragma unroll
+        for (int g = 0; g < WGS; ++g) {
+          if (!ok || k >= cnt[g]) continue;
+          if (!wait_flag(smem_u32(&S.rdy[g][s]), (par >> g) & 1u, err)) {
+            ok = false;
+            continue;
+          }
+          par ^= 1u << g;
+          fence_after_sync();
+          const WgBuffers &B = S.wb[g];
+          // operands: dW3^T = h2^T dL/do; dW2 = dL/da2^T [h1|1]; dW1 = dL/da1^T [x|1]
+          // (dL/da1 lives in the h2 buffer)
+          uint32_t sa, sb, a_lbo, b_lbo;
+          if (s == ST_DW3) {
+            sa = smem_u32(B.h2), a_lbo = 1280, sb = smem_u32(B.ob), b_lbo = 256;
+          } else if (s == ST_DW2) {
+            sa = smem_u32(B.a2b), a_lbo = 1024, sb = smem_u32(B.h1), b_lbo = 1280;
+          } else {
+            sa = smem_u32(B.h2), a_lbo = 1024, sb = smem_u32(B.a1), b_lbo = 256;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            mma_bf16(tmem + acc_col, smem_desc(sa + 2 * a_lbo * q, a_lbo, 128),
+                     smem_desc(sb + 2 * b_lbo * q, b_lbo, 128), id, (started || q > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&S.dwd[g][s]));
+          started = true;
+        }
+      }
+      if (started) {  // every weight-gradient MMA done before the sums are read
+        mma_commit(smem_u32(&S.drain[s]));
+        if (!mbar_wait_bounded(smem_u32(&S.drain[s]), 0, WAIT_LIMIT))
+          atomicOr(const_cast<int *>(err), 1);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- tile warpgroups
+    const int wg = warp >> 2;
+    const int r = tid & 127;
+    const bool leader = r == 0;
+    const uint32_t bar_id = 1 + wg;
+    WgBuffers &B = S.wb[wg];
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tm_wg = tmem + (uint32_t)(wg * WG_COLS);
+    const uint32_t tm_row = tm_wg + C_D + lane_off;
+    const uint32_t bar = smem_u32(&S.bar[wg]);
+    const uint32_t s_a1 = smem_u32(B.a1), s_h1 = smem_u32(B.h1), s_h2 = smem_u32(B.h2);
+    const uint32_t s_ob = smem_u32(B.ob), s_a2b = smem_u32(B.a2b);
+    const uint32_t s_w1 = smem_u32(S.w1), s_w2 = smem_u32(S.w2), s_w3 = smem_u32(S.w3);
+    const uint32_t s_w3t = smem_u32(S.w3t), s_w2t = smem_u32(S.w2t), s_w1t = smem_u32(S.w1t);
+    constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
+    unsigned char *a1b = B.h2;  // dL/da1 takes the h2 buffer once dW3 has read it
+    int t_begin, count;
+    range(wg, t_begin, count);
+    any_tiles = count > 0;
+    TilePos T;
+    T.x0 = (t_begin % tiles_x) * WG_THREADS;
+    T.y = (t_begin / tiles_x) % ny;
+    T.b = t_begin / (tiles_x * ny);
+    const float omega = p.omega;
+    uint32_t phase = 0, dpar = 0;  // own GEMMs; bit s: parity of dwd[wg][s]
+    bool pending = false;          // the leader has an own commit outstanding
+
+// the warpgroup's own GEMM: wait for its commit
+#define WAIT_OWN_OR_BREAK()                                                    \
+  if (!wg_wait(bar, phase, 0, 0, false, leader, bar_id, err)) break;            \
+  phase ^= 1;                                                                   \
+  pending = false;
+// all operand rows written: make them visible to the tensor core
+#define OPERANDS_READY()   \
+  fence_proxy_async();     \
+  fence_before_sync();     \
   named_barrier(bar_id, WG_THREADS);
 
-  for (int it = 0; it < count; ++it) {
-    const int x = T.x0 + r;
-    const bool active = x < nx;
-    const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x >= nx - 1 ? 0 : x + 1;
-    const float *gb = state + (size_t)T.b * Q * plane;
-    float d[Q], pb[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      d[i] = 0.f;
-      pb[i] = 0.f;
-    }
-    if (active) {
+    for (int it = 0; it < count; ++it) {
+      // the previous tile's dW2 and dW1 GEMMs read a1, h1, h2 and dL/da2
+      if (it > 0) {
+        if (!wg_wait(smem_u32(&S.dwd[wg][ST_DW2]), (dpar >> ST_DW2) & 1u,
+                     smem_u32(&S.dwd[wg][ST_DW1]), (dpar >> ST_DW1) & 1u, true, leader, bar_id,
+                     err))
+          break;
+        dpar ^= (1u << ST_DW2) | (1u << ST_DW1);
+      }
+      const int x = T.x0 + r;
+      const bool active = x < nx;
+      const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
+      const int xm = x == 0 ? nx - 1 : x - 1, xp = x >= nx - 1 ? 0 : x + 1;
+      float d[Q], pb[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
-        const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
-        d[i] = __ldg(gb + (size_t)i * plane + ys * nx + xs);
-        pb[i] = __ldg(lam_next + (size_t)T.b * Q * plane + (size_t)i * plane + T.y * nx + x);
+        d[i] = 0.f;
+        pb[i] = 0.f;
       }
-    }
-    // ---- forward recompute: moments, equilibrium, layer-1 operand
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    Moments m;
-    m.drho = drho;
-    m.rho = 1.0f + drho;
-    const float inv_rho = 1.0f / m.rho;
-    m.ux = jx * inv_rho;
-    m.uy = jy * inv_rho;
-    float deq[Q], xin[Q];
-    shifted_feq(m, deq);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
-    *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 0, K1)) =
-        make_uint4(pack_bf16x2(xin[0], xin[1]), pack_bf16x2(xin[2], xin[3]),
-                   pack_bf16x2(xin[4], xin[5]), pack_bf16x2(xin[6], xin[7]));
-    *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 8, K1)) =
-        make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
-    OPERANDS_READY()
-    if (leader) {
-      fence_after_sync();
-      mma_bf16(tm_wg + C_D, smem_desc(s_a1, 128, 16 * K1), smem_desc(s_w1, 128, 16 * K1), ID64, 0);
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    tanh_row(tm_row, B.h1, r, tm_wg + C_DH1 + lane_off);
-    OPERANDS_READY()
-    if (leader) {
-      fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg + C_D, smem_desc(s_h1 + 256 * s, 128, 16 * K2),
-                 smem_desc(s_w2 + 256 * s, 128, 16 * K2), ID64, s > 0);
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    tanh_row(tm_row, B.h2, r, tm_wg + C_DH2 + lane_off);
-    OPERANDS_READY()
-    if (leader) {
-      fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg + C_D, smem_desc(s_h2 + 256 * s, 128, 16 * K2),
-                 smem_desc(s_w3 + 256 * s, 128, 16 * K2), ID16, s > 0);
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    // ---- output of the network, then the reverse pass down to dL/do (FP32)
-    float oh[Q];
-    {
-      uint32_t ov[16];
-      tmem_ld16(tm_row, ov);
-      tmem_wait_ld();
-#pragma unroll
-      for (int i = 0; i < Q; ++i) oh[i] = __uint_as_float(ov[i]);
-      project9(oh);
-    }
-    // post = d + omega (deq - d) + rho omega ohat + fext(rho, u)
-    float fb[Q], deqb[Q], ob[Q];
-    float rhob = 0.f, uxb = 0.f, uyb = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      fb[i] = pb[i] * (1.0f - omega);
-      deqb[i] = pb[i] * omega;
-      ob[i] = m.rho * omega * pb[i];
-      rhob = fmaf(omega * pb[i], oh[i], rhob);
-    }
-    if (p.force) {
-      const float fx = __ldg(p.force + T.y);
-      const float sxv = m.ux + fx * inv_rho;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        float dr1, dx1, dy1, dr0, dx0, dy0;
-        feq_partials(m.rho, sxv, m.uy, i, dr1, dx1, dy1);
-        feq_partials(m.rho, m.ux, m.uy, i, dr0, dx0, dy0);
-        rhob += pb[i] * ((dr1 - dx1 * fx * inv_rho * inv_rho) - dr0);
-        uxb += pb[i] * (dx1 - dx0);
-        uyb += pb[i] * (dy1 - dy0);
-      }
-    }
-    project9(ob);  // dL/do = P dL/dohat (P symmetric)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) db3[i] += ob[i];
-    *reinterpret_cast<uint4 *>(B.ob + canon_offset(r, 0, 16)) =
-        make_uint4(pack_bf16x2(ob[0], ob[1]), pack_bf16x2(ob[2], ob[3]),
-                   pack_bf16x2(ob[4], ob[5]), pack_bf16x2(ob[6], ob[7]));
-    *reinterpret_cast<uint4 *>(B.ob + canon_offset(r, 8, 16)) =
-        make_uint4(pack_bf16x2(ob[8], 0.0f), 0u, 0u, 0u);
-    OPERANDS_READY()
-    if (leader) {  // dL/da2 (before the tanh derivative) = dL/do . W3
-      fence_after_sync();
-      mma_bf16(tm_wg + C_D, smem_desc(s_ob, 128, 256), smem_desc(s_w3t, 128, 256), ID64, 0);
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    dtanh_row(tm_row, tm_wg + C_DH2 + lane_off, B.a2b, r);
-    OPERANDS_READY()
-    if (leader) {  // dL/da1 (before the tanh derivative) = dL/da2 . W2
-      fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        mma_bf16(tm_wg + C_D, smem_desc(s_a2b + 256 * s, 128, 1024),
-                 smem_desc(s_w2t + 256 * s, 128, 1024), ID64, s > 0);
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    dtanh_row(tm_row, tm_wg + C_DH1 + lane_off, B.a1b, r);
-    OPERANDS_READY()
-    if (leader) {
-      fence_after_sync();
-      // dL/dx = dL/da1 . W1
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        mma_bf16(tm_wg + C_D, smem_desc(s_a1b + 256 * s, 128, 1024),
-                 smem_desc(s_w1t + 256 * s, 128, 1024), ID16, s > 0);
-      // weight gradients: reduction over the 128 nodes of the tile, 16 per MMA
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
-        mma_bf16(tm_wg + C_DW2, smem_desc(s_a2b + 2 * 1024 * s, 1024, 128),
-                 smem_desc(s_h1 + 2 * 1280 * s, 1280, 128), IDW80, acc);
-        mma_bf16(tm_wg + C_DW1, smem_desc(s_a1b + 2 * 1024 * s, 1024, 128),
-                 smem_desc(s_a1 + 2 * 256 * s, 256, 128), IDW16, acc);
-        mma_bf16(tm_wg + C_DW3, smem_desc(s_h2 + 2 * 1280 * s, 1280, 128),
-                 smem_desc(s_ob + 2 * 256 * s, 256, 128), IDW16, acc);
-      }
-      mma_commit(bar);
-    }
-    WAIT_OR_BREAK()
-    // ---- dL/dx -> rest of the chain rule (FP32), scatter lam to x - c_i
-    {
-      uint32_t xv[16];
-      tmem_ld16(tm_row, xv);
-      tmem_wait_ld();
-      float xb[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) xb[i] = __uint_as_float(xv[i]);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        fb[i] += xb[i] * inv_rho;
-        deqb[i] -= xb[i] * inv_rho;
-        rhob -= xb[i] * xin[i] * inv_rho;
-      }
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        float dr, dux, duy;
-        feq_partials(m.rho, m.ux, m.uy, i, dr, dux, duy);
-        rhob = fmaf(deqb[i], dr, rhob);
-        uxb = fmaf(deqb[i], dux, uxb);
-        uyb = fmaf(deqb[i], duy, uyb);
-      }
-      const float jxb = uxb * inv_rho, jyb = uyb * inv_rho;
-      rhob -= (uxb * m.ux + uyb * m.uy) * inv_rho;
       if (active) {
-        float *lo = lam_out + (size_t)T.b * Q * plane;
+        const float *gb = state + (size_t)T.b * Q * plane;
+        const float *lb = lam_next + (size_t)T.b * Q * plane + T.y * nx + x;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          const float v = fb[i] + rhob + (float)cx(i) * jxb + (float)cy(i) * jyb;
           const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
           const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
-          lo[(size_t)i * plane + ys * nx + xs] = v;  // lam_i(x - c_i)
+          d[i] = __ldg(gb + (size_t)i * plane + ys * nx + xs);
+          pb[i] = __ldg(lb + (size_t)i * plane);
+        }
+      }
+      // ---- forward recompute: moments, equilibrium, layer-1 operand
+      Moments m;
+      float inv_rho;
+      {
+        const float drho =
+            ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+        const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+        const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+        m.drho = drho;
+        m.rho = 1.0f + drho;
+        inv_rho = 1.0f / m.rho;
+        m.ux = jx * inv_rho;
+        m.uy = jy * inv_rho;
+        float deq[Q], xin[Q];
+        shifted_feq(m, deq);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+        *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 0, K1)) =
+            make_uint4(pack_bf16x2(xin[0], xin[1]), pack_bf16x2(xin[2], xin[3]),
+                       pack_bf16x2(xin[4], xin[5]), pack_bf16x2(xin[6], xin[7]));
+        *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 8, K1)) =
+            make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
+      }
+      OPERANDS_READY()
+      if (leader) {
+        fence_after_sync();
+        mma_bf16(tm_wg + C_D, smem_desc(s_a1, 128, 16 * K1), smem_desc(s_w1, 128, 16 * K1), ID64,
+                 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      tanh_row(tm_row, B.h1, r, tm_wg + C_DH1 + lane_off);
+      OPERANDS_READY()
+      if (leader) {
+        fence_after_sync();
+#pragma unroll
+        for (int s = 0; s < K2 / 16; ++s)
+          mma_bf16(tm_wg + C_D, smem_desc(s_h1 + 256 * s, 128, 16 * K2),
+                   smem_desc(s_w2 + 256 * s, 128, 16 * K2), ID64, s > 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      tanh_row(tm_row, B.h2, r, tm_wg + C_DH2 + lane_off);
+      OPERANDS_READY()
+      if (leader) {
+        fence_after_sync();
+#pragma unroll
+        for (int s = 0; s < K2 / 16; ++s)
+          mma_bf16(tm_wg + C_D, smem_desc(s_h2 + 256 * s, 128, 16 * K2),
+                   smem_desc(s_w3 + 256 * s, 128, 16 * K2), ID16, s > 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      // ---- output of the network, then the reverse pass down to dL/do (FP32)
+      // post = d + omega (deq - d) + rho omega ohat + fext(rho, u)
+      float rhob = 0.f, uxb = 0.f, uyb = 0.f;
+      {
+        float oh[Q], ob[Q];
+        uint32_t ov[16];
+        tmem_ld16(tm_row, ov);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) oh[i] = __uint_as_float(ov[i]);
+        project9(oh);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          ob[i] = m.rho * omega * pb[i];
+          rhob = fmaf(omega * pb[i], oh[i], rhob);
+        }
+        if (p.force) {
+          const float fx = __ldg(p.force + T.y);
+          const float sxv = m.ux + fx * inv_rho;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            float dr1, dx1, dy1, dr0, dx0, dy0;
+            feq_partials(m.rho, sxv, m.uy, i, dr1, dx1, dy1);
+            feq_partials(m.rho, m.ux, m.uy, i, dr0, dx0, dy0);
+            rhob += pb[i] * ((dr1 - dx1 * fx * inv_rho * inv_rho) - dr0);
+            uxb += pb[i] * (dx1 - dx0);
+            uyb += pb[i] * (dy1 - dy0);
+          }
+        }
+        project9(ob);  // dL/do = P dL/dohat (P symmetric)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) db3[i] += ob[i];
+        *reinterpret_cast<uint4 *>(B.ob + canon_offset(r, 0, 16)) =
+            make_uint4(pack_bf16x2(ob[0], ob[1]), pack_bf16x2(ob[2], ob[3]),
+                       pack_bf16x2(ob[4], ob[5]), pack_bf16x2(ob[6], ob[7]));
+        *reinterpret_cast<uint4 *>(B.ob + canon_offset(r, 8, 16)) =
+            make_uint4(pack_bf16x2(ob[8], 0.0f), 0u, 0u, 0u);
+      }
+      OPERANDS_READY()
+      if (leader) {
+        mbar_arrive(smem_u32(&S.rdy[wg][ST_DW3]));  // h2 and dL/do complete
+        fence_after_sync();
+        // dL/da2 (before the tanh derivative) = dL/do . W3
+        mma_bf16(tm_wg + C_D, smem_desc(s_ob, 128, 256), smem_desc(s_w3t, 128, 256), ID64, 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      dtanh_row(tm_row, tm_wg + C_DH2 + lane_off, B.a2b, r);
+      OPERANDS_READY()
+      if (leader) {
+        mbar_arrive(smem_u32(&S.rdy[wg][ST_DW2]));  // dL/da2 and h1 complete
+        fence_after_sync();
+        // dL/da1 (before the tanh derivative) = dL/da2 . W2
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          mma_bf16(tm_wg + C_D, smem_desc(s_a2b + 256 * s, 128, 1024),
+                   smem_desc(s_w2t + 256 * s, 128, 1024), ID64, s > 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      // own GEMM, and dW3 (it reads h2, which dL/da1 overwrites next)
+      if (!wg_wait(bar, phase, smem_u32(&S.dwd[wg][ST_DW3]), (dpar >> ST_DW3) & 1u, true, leader,
+                   bar_id, err))
+        break;
+      phase ^= 1;
+      pending = false;
+      dpar ^= 1u << ST_DW3;
+      dtanh_row(tm_row, tm_wg + C_DH1 + lane_off, a1b, r);
+      OPERANDS_READY()
+      if (leader) {
+        mbar_arrive(smem_u32(&S.rdy[wg][ST_DW1]));  // dL/da1 and x complete
+        fence_after_sync();
+        // dL/dx = dL/da1 . W1
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          mma_bf16(tm_wg + C_D, smem_desc(s_h2 + 256 * s, 128, 1024),
+                   smem_desc(s_w1t + 256 * s, 128, 1024), ID16, s > 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      // ---- dL/dx -> rest of the chain rule (FP32), scatter lam to x - c_i
+      {
+        uint32_t xv[16];
+        tmem_ld16(tm_row, xv);
+        tmem_wait_ld();
+        float deq[Q];
+        shifted_feq(m, deq);
+        float fb[Q], deqb[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const float xb = __uint_as_float(xv[i]) * inv_rho;
+          const float xin = (d[i] - deq[i]) * inv_rho;
+          fb[i] = pb[i] * (1.0f - omega) + xb;
+          deqb[i] = pb[i] * omega - xb;
+          rhob -= xb * xin;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          float dr, dux, duy;
+          feq_partials(m.rho, m.ux, m.uy, i, dr, dux, duy);
+          rhob = fmaf(deqb[i], dr, rhob);
+          uxb = fmaf(deqb[i], dux, uxb);
+          uyb = fmaf(deqb[i], duy, uyb);
+        }
+        const float jxb = uxb * inv_rho, jyb = uyb * inv_rho;
+        rhob -= (uxb * m.ux + uyb * m.uy) * inv_rho;
+        if (active) {
+          float *lo = lam_out + (size_t)T.b * Q * plane;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const float v = fb[i] + rhob + (float)cx(i) * jxb + (float)cy(i) * jyb;
+            const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
+            const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
+            lo[(size_t)i * plane + ys * nx + xs] = v;  // lam_i(x - c_i)
+          }
+        }
+      }
+      T.advance(nx, ny);
+    }
+#undef WAIT_OWN_OR_BREAK
+#undef OPERANDS_READY
+    // after a time-out: let this warpgroup's own MMAs finish before the
+    // tensor memory is freed
+    if (leader && pending) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+  }
+
+  // ---- db3: per-warp sums of dL/do
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float v = db3[i];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0 && warp < DW_WARP) S.db3[warp][i] = v;
+  }
+  // ---- teardown: every role has left its loop, the issuer has drained
+  fence_before_sync();
+  const int any = __syncthreads_or(any_tiles ? 1 : 0);
+  fence_after_sync();
+  const bool have = any && !S.err;
+  float *row = partials + (size_t)blockIdx.x * NPARAMS;
+  if (warp < 4) {
+    // M = 64 accumulators: row j lives in lane 32 (j / 16) + j % 16
+    const uint32_t lo = (uint32_t)(32 * warp) << 16;
+    const int j = 16 * warp + lane;
+#pragma unroll 1
+    for (int c = 0; c < 7; ++c) {
+      uint32_t v[16];
+      const uint32_t col = c < 5 ? C_DW2 + 16 * c : (c == 5 ? C_DW1 : C_DW3);
+      tmem_ld16(tmem + col + lo, v);
+      tmem_wait_ld();
+      if (lane < 16) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float g = have ? __uint_as_float(v[k]) : 0.f;
+          float *dst = nullptr;
+          if (c < 4) {
+            dst = row + OFF_W2 + j * HIDDEN + 16 * c + k;
+          } else if (c == 4) {
+            if (k == 0) dst = row + OFF_B2 + j;
+          } else if (c == 5) {
+            if (k < 9) dst = row + OFF_W1 + j * 9 + k;
+            else if (k == 9) dst = row + OFF_B1 + j;
+          } else {
+            if (k < 9) dst = row + OFF_W3 + k * HIDDEN + j;
+          }
+          if (dst) *dst = accumulate ? *dst + g : g;
         }
       }
     }
-    T.advance(nx, ny);
   }
-#undef WAIT_OR_BREAK
-#undef OPERANDS_READY
-
-  if (leader && fail) {
-    atomicOr(timeout_flag, 1);
-    mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-  }
-  // ---- this warpgroup's weight-gradient sums -> its row of partial sums
-  float *row = partials + (size_t)gwg * NPARAMS;
-  const bool have = count > 0 && !fail;
-  {
-    // db3: reduce the per-node sums of dL/do over the warpgroup
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float v = db3[i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if ((r & 31) == 0) S.db3[wg][warp_in_wg][i] = v;
-    }
-  }
-  fence_after_sync();
-  // M = 64 accumulators: row j lives in lane 32 (j / 16) + j % 16
-  const int lane = r & 31;
-  const int j = 16 * warp_in_wg + lane;
-  uint32_t v2[80], v1[16], v3[16];
-  tmem_ld32(tm_wg + C_DW2 + lane_off, *reinterpret_cast<uint32_t(*)[32]>(v2));
-  tmem_ld32(tm_wg + C_DW2 + 32 + lane_off, *reinterpret_cast<uint32_t(*)[32]>(v2 + 32));
-  tmem_ld16(tm_wg + C_DW2 + 64 + lane_off, *reinterpret_cast<uint32_t(*)[16]>(v2 + 64));
-  tmem_ld16(tm_wg + C_DW1 + lane_off, v1);
-  tmem_ld16(tm_wg + C_DW3 + lane_off, v3);
-  tmem_wait_ld();
-  named_barrier(bar_id, WG_THREADS);  // db3 partial sums visible
-  if (lane < 16) {
-    for (int k = 0; k < HIDDEN; ++k) {
-      const float g = have ? __uint_as_float(v2[k]) : 0.f;
-      float *dst = row + OFF_W2 + j * HIDDEN + k;
-      *dst = accumulate ? *dst + g : g;
-    }
-    {
-      const float g = have ? __uint_as_float(v2[64]) : 0.f;
-      row[OFF_B2 + j] = accumulate ? row[OFF_B2 + j] + g : g;
-    }
-    for (int i = 0; i < 9; ++i) {
-      const float g = have ? __uint_as_float(v1[i]) : 0.f;
-      float *dst = row + OFF_W1 + j * 9 + i;
-      *dst = accumulate ? *dst + g : g;
-      const float g3 = have ? __uint_as_float(v3[i]) : 0.f;
-      float *dst3 = row + OFF_W3 + i * HIDDEN + j;
-      *dst3 = accumulate ? *dst3 + g3 : g3;
-    }
-    {
-      const float g = have ? __uint_as_float(v1[9]) : 0.f;
-      row[OFF_B1 + j] = accumulate ? row[OFF_B1 + j] + g : g;
-    }
-  }
-  if (r < 9) {
-    const float g = S.db3[wg][0][r] + S.db3[wg][1][r] + S.db3[wg][2][r] + S.db3[wg][3][r];
-    row[OFF_B3 + r] = accumulate ? row[OFF_B3 + r] + g : g;
+  if (tid < 9) {
+    float g = 0.f;
+    for (int k = 0; k < WGS * 4; ++k) g += S.db3[k][tid];
+    if (!have) g = 0.f;
+    row[OFF_B3 + tid] = accumulate ? row[OFF_B3 + tid] + g : g;
   }
   fence_before_sync();
   __syncthreads();
-  if (tid < 32) tmem_dealloc(S.taddr, TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (tid == 0 && S.err) atomicOr(timeout_flag, 1);
 }
 
 }  // namespace
@@ -523,7 +676,7 @@ int adjoint_tc_rows(const Grid &g, int sms) {
   const long long tiles = (long long)((g.nx + WG_THREADS - 1) / WG_THREADS) * g.ny * g.batch;
   long long ctas = (tiles + WGS - 1) / WGS;
   if (ctas > sms) ctas = sms;
-  return (int)(ctas * WGS);
+  return (int)ctas;  // one row of partial sums per CTA
 }
 
 cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *lam_next,
@@ -538,9 +691,8 @@ cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *
     attr_set = true;
   }
   if ((long long)g.nx * g.ny * g.batch * Q >= (1LL << 31)) return cudaErrorInvalidValue;
-  k_adjoint_tc<<<rows / WGS, THREADS, SMEM_BYTES, s>>>(state_n, lam_next, lam_out, g.nx, g.ny,
-                                                       g.batch, p, w, dw_partials, accumulate,
-                                                       timeout_flag);
+  k_adjoint_tc<<<rows, THREADS, SMEM_BYTES, s>>>(state_n, lam_next, lam_out, g.nx, g.ny, g.batch,
+                                                 p, w, dw_partials, accumulate, timeout_flag);
   return cudaGetLastError();
 }
 
