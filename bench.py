@@ -489,7 +489,8 @@ def run_reference(args):
 
 def run_profile_case(args):
     """Small case for ncu: `--steps` steps of one collision kind on a
-    `--grid` x `--grid` lattice (no JSON line)."""
+    `--grid` x `--grid` lattice, or one training step (`adjoint_bf16`); no JSON
+    line."""
     import torch
     from paper_2403_18466_gb300 import inputs, lbm
     dev = torch.device("cuda:0")
@@ -507,6 +508,28 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         rc = lat.status()
         print(f"profile case {args.profile} {n}^3 x {args.steps}: {lbm.lbm_strerror(rc)}")
+        if rc != lbm.LBM_OK:
+            sys.exit(1)
+        return
+    if args.profile == "adjoint_bf16":
+        # one unrolled training step of the tensor-core pair: 32 trajectories
+        # of --grid^2, --steps LES steps, checkpoint every 4
+        B, n, L = 32, args.grid, args.steps
+        lat = lbm.Lattice(n, n, B, tau=0.500375, force_amp=8e-5, force_mode=4, device=dev)
+        ux = torch.tensor(inputs.noise((B, n, n), 5, 0.02), dtype=torch.float32, device=dev)
+        uy = torch.tensor(inputs.noise((B, n, n), 6, 0.02), dtype=torch.float32, device=dev)
+        lat.init_equilibrium(torch.ones((B, n, n), device=dev), ux, uy)
+        theta = torch.tensor(inputs.xavier_mlp(3, out_scale=0.01), dtype=torch.float32,
+                             device=dev)
+        w = lbm.weights_struct(theta)
+        ws = torch.empty(lat.record_bytes(L, 4) // 4, dtype=torch.float32, device=dev)
+        dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=dev)
+        lat.forward_record(L, 4, w, ws, "bf16")
+        _, g = lat.velocity_loss(ux, uy)
+        lat.backward(g, w, ws, dW, None, "bf16")
+        torch.cuda.synchronize()
+        rc = lat.status()
+        print(f"profile case adjoint_bf16 32 x {n}^2 x {L}: {lbm.lbm_strerror(rc)}")
         if rc != lbm.LBM_OK:
             sys.exit(1)
         return
@@ -552,7 +575,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default=None,
                     choices=["bgk", "smag", "mlp_bf16", "mlp_f32", "d3_bgk", "d3_smag",
-                             "d3_mlp_bf16", "d3_mlp_f32"],
+                             "d3_mlp_bf16", "d3_mlp_f32", "adjoint_bf16"],
                     help="run a small case of one kernel for ncu and exit")
     ap.add_argument("--grid", type=int, default=2048)
     args = ap.parse_args()
