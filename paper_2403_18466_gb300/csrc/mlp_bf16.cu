@@ -29,7 +29,13 @@
 // sustains ~0.24 tanh warp instructions per cycle per SM when 16 warps per SM
 // feed it, so the 128 activations of a node cap the step near 37 G nodes/s
 // however the GEMMs and memory traffic are scheduled (HBM alone would allow
-// 94 G); with fewer warps in their tanh phase at once it reaches less.
+// 94 G); with fewer warps in their tanh phase at once it reaches less.  Hence
+// one CTA per SM of eight warpgroups (32 warps, 64 registers per thread; all
+// 512 tensor-memory columns, 207 KB of shared memory): more warpgroups per SM
+// keep more of them in their tanh epilogues at any time (measured at 4096^2:
+// 4 warpgroups per SM 19.8 G nodes/s, 6: 23.6 G, 8: 24.3 G).  The tanh
+// epilogue works through 16 columns at a time to stay within that register
+// budget.
 //
 // Synchronisation per warpgroup: operand rows written by all 128 threads
 // -> fence.proxy.async + named barrier -> one thread issues the MMAs and
@@ -51,10 +57,10 @@ using namespace umma;
 
 constexpr int WG_THREADS = 128;
 #ifndef LBM_BF16_WGS
-#define LBM_BF16_WGS 2
+#define LBM_BF16_WGS 8
 #endif
 #ifndef LBM_BF16_CTAS_PER_SM
-#define LBM_BF16_CTAS_PER_SM 2
+#define LBM_BF16_CTAS_PER_SM 1
 #endif
 constexpr int WGS = LBM_BF16_WGS;                  // warpgroups per CTA
 constexpr int CTAS_PER_SM = LBM_BF16_CTAS_PER_SM;  // resident CTAs per SM
@@ -146,16 +152,16 @@ __device__ __forceinline__ void pull_node(const float *__restrict__ in, int plan
 // pairs, write them as K columns 0..63 of the thread's layer-2/3 operand row.
 __device__ __forceinline__ void tanh_row_to_operand(uint32_t tm_row, unsigned char *a23, int r) {
 #pragma unroll
-  for (int c = 0; c < HIDDEN; c += 32) {
-    uint32_t v[32];
-    tmem_ld32(tm_row + c, v);
+  for (int c = 0; c < HIDDEN; c += 16) {
+    uint32_t v[16];
+    tmem_ld16(tm_row + c, v);
     tmem_wait_ld();
-    uint32_t p[16];
+    uint32_t p[8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
+    for (int q = 0; q < 8; ++q)
       p[q] = tanh_bf16x2(pack_bf16x2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])));
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 2; ++q)
       *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8 * q, K2)) =
           make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
@@ -262,11 +268,13 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     m.ux = jx * inv_rho;
     m.uy = jy * inv_rho;
     flag_unstable(active && is_unstable(m), flag);
-    float deq[Q];
-    shifted_feq(m, deq);
     float xin[Q];
+    {
+      float deq[Q];
+      shifted_feq(m, deq);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+      for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+    }
     *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
         make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
                    pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
@@ -340,23 +348,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
       for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
       project9(o);
       if (active) {
+        float deq[Q];
+        shifted_feq(m, deq);
         const float rw = m.rho * omega;
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = fmaf(omega, deq[i] - d[i], d[i]) + rw * o[i];
-        if (p.force) {
-          // EDM force (Eq. S5) for F = (fx, 0), cancellation-free form
-          const float fx = __ldg(p.force + T.y);
-          const float sx = 2.0f * m.ux + fx * inv_rho;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            if (cx(i) == 0) {
-              d[i] -= wf(i) * fx * sx * 1.5f;
-            } else {
-              const float cs = (float)cx(i) * sx + (float)cy(i) * 2.0f * m.uy;
-              d[i] += wf(i) * fx * ((float)cx(i) * (3.0f + 4.5f * cs) - 1.5f * sx);
-            }
-          }
-        }
+        // EDM force (Eq. S5) for F = (fx, 0): the helper the BGK kernel uses,
+        // so that a zero output layer reproduces BGK bit for bit
+        if (p.force) add_edm_force_x(m, __ldg(p.force + T.y), d);
         float *ob = out + (size_t)T.b * Q * plane + T.y * nx + x;
 #pragma unroll
         for (int i = 0; i < Q; ++i) ob[(size_t)i * plane] = d[i];
