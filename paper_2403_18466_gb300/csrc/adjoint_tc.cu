@@ -103,14 +103,43 @@ __device__ __forceinline__ void project9(float o[Q]) {
   for (int i = 0; i < Q; ++i) o[i] += k1 + (float)cx(i) * k2 + (float)cy(i) * k3;
 }
 
-// Partial derivatives of feq_i(rho, u) = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2).
-__device__ __forceinline__ void feq_partials(float rho, float ux, float uy, int i, float &dr,
-                                             float &dux, float &duy) {
-  const float cu = (float)cx(i) * ux + (float)cy(i) * uy;
+// Sums of a per-direction vector g against the partial derivatives of
+// feq_i(rho, u) = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2).  feq_i is
+// quadratic in c_i, so every such sum is a combination of the six weighted
+// moments sum_i w_i g_i c_i^a c_i^b (monomials 1, c_x, c_y, c_x^2, c_x c_y,
+// c_y^2): about 40 operations for the moments and 25 per velocity, instead of
+// the 9 x 20 of a sum over directions.
+struct GMom {
+  float g0, gx, gy, gxx, gxy, gyy;
+};
+// Adds w_i g times the monomials of direction i (compile-time i).
+__device__ __forceinline__ void gmom_add(GMom &s, int i, float g) {
+  const float v = wf(i) * g;
+  s.g0 += v;
+  if (cx(i) != 0) {
+    s.gx += cx(i) > 0 ? v : -v;
+    s.gxx += v;
+  }
+  if (cy(i) != 0) {
+    s.gy += cy(i) > 0 ? v : -v;
+    s.gyy += v;
+  }
+  if (cx(i) * cy(i) != 0) s.gxy += cx(i) * cy(i) > 0 ? v : -v;
+}
+__device__ __forceinline__ GMom weighted_moments(const float g[Q]) {
+  GMom s = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) gmom_add(s, i, g[i]);
+  return s;
+}
+// sum_i g_i dfeq_i/drho, dfeq_i/du_x, dfeq_i/du_y at (rho, ux, uy)
+__device__ __forceinline__ void feq_vjp(const GMom &s, float rho, float ux, float uy, float &sr,
+                                        float &sx, float &sy) {
   const float usq = ux * ux + uy * uy;
-  dr = wf(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
-  dux = wf(i) * rho * (3.0f * (float)cx(i) + 9.0f * cu * (float)cx(i) - 3.0f * ux);
-  duy = wf(i) * rho * (3.0f * (float)cy(i) + 9.0f * cu * (float)cy(i) - 3.0f * uy);
+  sr = s.g0 * (1.0f - 1.5f * usq) + 3.0f * (ux * s.gx + uy * s.gy) +
+       4.5f * (ux * ux * s.gxx + 2.0f * ux * uy * s.gxy + uy * uy * s.gyy);
+  sx = rho * (3.0f * s.gx + 9.0f * (ux * s.gxx + uy * s.gxy) - 3.0f * ux * s.g0);
+  sy = rho * (3.0f * s.gy + 9.0f * (ux * s.gxy + uy * s.gyy) - 3.0f * uy * s.g0);
 }
 
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
@@ -504,17 +533,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           rhob = fmaf(omega * pb[i], oh[i], rhob);
         }
         if (p.force) {
+          // f_ext = feq(rho, u + a) - feq(rho, u), a = (fx/rho, 0): the
+          // differences of the two sums, written without cancellation
+          // (s = 2 u_x + a_x), and the rho-dependence of a
           const float fx = __ldg(p.force + T.y);
-          const float sxv = m.ux + fx * inv_rho;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            float dr1, dx1, dy1, dr0, dx0, dy0;
-            feq_partials(m.rho, sxv, m.uy, i, dr1, dx1, dy1);
-            feq_partials(m.rho, m.ux, m.uy, i, dr0, dx0, dy0);
-            rhob += pb[i] * ((dr1 - dx1 * fx * inv_rho * inv_rho) - dr0);
-            uxb += pb[i] * (dx1 - dx0);
-            uyb += pb[i] * (dy1 - dy0);
-          }
+          const float ax = fx * inv_rho;
+          const float sxs = 2.0f * m.ux + ax, uxs = m.ux + ax;
+          const GMom q = weighted_moments(pb);
+          const float sx1 =
+              m.rho * (3.0f * q.gx + 9.0f * (uxs * q.gxx + m.uy * q.gxy) - 3.0f * uxs * q.g0);
+          rhob += ax * (3.0f * q.gx + 4.5f * (sxs * q.gxx + 2.0f * m.uy * q.gxy) -
+                        1.5f * sxs * q.g0) -
+                  ax * inv_rho * sx1;
+          uxb += m.rho * ax * (9.0f * q.gxx - 3.0f * q.g0);
+          uyb += m.rho * ax * 9.0f * q.gxy;
         }
         project9(ob);  // dL/do = P dL/dohat (P symmetric)
 #pragma unroll
@@ -576,22 +608,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_wait_ld();
         float deq[Q];
         shifted_feq(m, deq);
-        float fb[Q], deqb[Q];
+        float fb[Q];
+        GMom q = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // moments of dL/dfeq
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const float xb = __uint_as_float(xv[i]) * inv_rho;
           const float xin = (d[i] - deq[i]) * inv_rho;
           fb[i] = pb[i] * (1.0f - omega) + xb;
-          deqb[i] = pb[i] * omega - xb;
+          gmom_add(q, i, pb[i] * omega - xb);
           rhob -= xb * xin;
         }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          float dr, dux, duy;
-          feq_partials(m.rho, m.ux, m.uy, i, dr, dux, duy);
-          rhob = fmaf(deqb[i], dr, rhob);
-          uxb = fmaf(deqb[i], dux, uxb);
-          uyb = fmaf(deqb[i], duy, uyb);
+        {
+          float sr, sx, sy;
+          feq_vjp(q, m.rho, m.ux, m.uy, sr, sx, sy);
+          rhob += sr;
+          uxb += sx;
+          uyb += sy;
         }
         const float jxb = uxb * inv_rho, jyb = uyb * inv_rho;
         rhob -= (uxb * m.ux + uyb * m.uy) * inv_rho;
