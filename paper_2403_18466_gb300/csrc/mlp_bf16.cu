@@ -22,7 +22,8 @@
 // layers each thread reads its own row back with tcgen05.ld, rounds pairs to
 // bf16x2 and applies the hardware tanh on the packed pairs, and writes the
 // next operand row.  The populations of the next tile are loaded while the
-// current tile's three GEMMs run.
+// current tile's GEMMs run, and its layer-1 operand is written while the
+// third GEMM runs (layer 1 has read its operand by then).
 //
 // Binding unit: the XU (MUFU) pipe.  Measured on this GPU with the
 // epilogue's instruction mix (cvt + tanh.approx.bf16x2 per pair), the XU
@@ -167,6 +168,41 @@ __device__ __forceinline__ void tanh_row_to_operand(uint32_t tm_row, unsigned ch
   }
 }
 
+// Moments of shifted populations, reciprocal of rho rounded to nearest: the
+// same arithmetic wherever a tile's moments are needed.
+__device__ __forceinline__ Moments moments_rn(const float d[Q], float &inv_rho) {
+  Moments m;
+  m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+  const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+  const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+  m.rho = 1.0f + m.drho;
+  inv_rho = __frcp_rn(m.rho);
+  m.ux = jx * inv_rho;
+  m.uy = jy * inv_rho;
+  return m;
+}
+
+// x = (f - feq)/rho of this thread's node -> row r of the layer-1 operand (9
+// inputs, the constant-1 bias column, zeros); flags an unstable node.
+__device__ __forceinline__ void prep_x(const float d[Q], bool active, unsigned char *a1, int r,
+                                       int *flag) {
+  float inv_rho;
+  const Moments m = moments_rn(d, inv_rho);
+  flag_unstable(active && is_unstable(m), flag);
+  float xin[Q];
+  {
+    float deq[Q];
+    shifted_feq(m, deq);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+  }
+  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
+      make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
+                 pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
+  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
+      make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
+}
+
 template <int DTYPE>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     k_step_mlp_bf16(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
@@ -252,34 +288,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] = 0.f;
   if (count > 0 && T.x0 + r < nx) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
+  if (count > 0) prep_x(d, T.x0 + r < nx, a1, r, flag);
 
   for (int it = 0; it < count; ++it) {
     const int x = T.x0 + r;
     const bool active = x < nx;
 
-    // ---- per-node FP32 pre-processing, layer-1 operand row
-    const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    Moments m;
-    m.drho = drho;
-    m.rho = 1.0f + drho;
-    const float inv_rho = __frcp_rn(m.rho);
-    m.ux = jx * inv_rho;
-    m.uy = jy * inv_rho;
-    flag_unstable(active && is_unstable(m), flag);
-    float xin[Q];
-    {
-      float deq[Q];
-      shifted_feq(m, deq);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
-    }
-    *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
-        make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
-                   pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
-    *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
-        make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
+    // ---- the tile's layer-1 operand rows are written (before the loop, or
+    // during the previous tile's third GEMM)
     fence_proxy_async();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
@@ -334,6 +350,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
       mma_commit(bar);
     }
 
+    // ---- the next tile's layer-1 operand while layer 3 runs (layer 1 of this
+    // tile has completed, so a1 is free)
+    if (it + 1 < count) prep_x(dn, N.x0 + r < nx, a1, r, flag);
+
     // ---- layer 3 epilogue: projection, BGK + learned correction + force, store
     if (leader) fail = !wait_mma(bar, phase);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
@@ -348,6 +368,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
       for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
       project9(o);
       if (active) {
+        float inv_rho;
+        const Moments m = moments_rn(d, inv_rho);
         float deq[Q];
         shifted_feq(m, deq);
         const float rw = m.rho * omega;
