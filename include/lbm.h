@@ -45,7 +45,7 @@ extern "C" {
 #define LBM_OK 0
 #define LBM_ERR_ARG (-1)         /* invalid argument (null pointer, size, kind) */
 #define LBM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
-#define LBM_ERR_UNSUPPORTED (-3) /* valid but not supported by this build */
+#define LBM_ERR_UNSUPPORTED (-3) /* valid but not supported by this library */
 #define LBM_ERR_UNSTABLE (-4)    /* a node reached |u| >= 0.4 or a non-finite value */
 #define LBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
 

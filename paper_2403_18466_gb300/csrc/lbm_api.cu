@@ -135,7 +135,7 @@ const char *lbm_strerror(int code) {
     case LBM_OK: return "ok";
     case LBM_ERR_ARG: return "invalid argument";
     case LBM_ERR_CUDA: return "CUDA runtime error";
-    case LBM_ERR_UNSUPPORTED: return "unsupported by this build";
+    case LBM_ERR_UNSUPPORTED: return "not supported by this library";
     case LBM_ERR_UNSTABLE: return "unstable: |u| >= 0.4 or non-finite velocity";
     case LBM_ERR_TIMEOUT: return "a bounded device wait gave up";
   }

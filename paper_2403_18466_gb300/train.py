@@ -7,7 +7,7 @@ and either the velocity form or the population form of Eq. S13), backpropagate
 through all steps with the library's hand-written adjoint (tensor-core pair by
 default, FP32 CUDA-core pair on request), and take an Adam step (learning rate 1e-4, weight decay 1e-6, Tab. S1).  Plain BGK and
 Smagorinsky-BGK LES from the same initial states are evaluated with the same
-loss as the baselines the learned collision is judged against.
+loss as the baselines the learned collision is compared with.
 
     python -m paper_2403_18466_gb300.train --epochs 200
 """
