@@ -248,3 +248,55 @@ def test_a_posteriori_evaluation_runs(lbm):
     # the Smagorinsky LES is stable at these parameters
     assert res["status"]["smag"] == lbm.lbm_strerror(lbm.LBM_OK) and res["unstable_at"]["smag"] is None
     assert len(res["final_spectra"]["dns"]) == 256 // 8 // 2 + 1
+
+
+def test_full_size_training_step_gradients(lbm):
+    """The training step at the benchmark's size (32 trajectories of 256², 16 LES
+    steps, checkpoint every 4, tau' = 0.500375, F' = 8e-5 with m = 4, velocity
+    loss), where the oracle would take too long: properties that hold at any
+    size.  (i) The FP32 pair's gradient along a random unit direction d agrees
+    with central differences of the FP32 forward, eps = 1e-2: the truncation
+    error is O(eps^2) relative and the FP64 loss sums keep the rounding noise of
+    the difference near 1e-9 relative, so 2e-3 relative covers both (measured
+    2e-5 on GB300).  (ii) The tensor-core pair's gradient, which carries bf16
+    rounding of h, 1 - h^2, dL/do and dL/da at every node and step, is within
+    the tensor-core adjoint's tolerance of the other tests, 5e-2 relative L2
+    (2.3e-2 for one step by a numpy emulation of those roundings on a state far
+    from equilibrium; measured 2.3e-3 here), of the FP32 pair's and points the
+    same way (cosine >= 0.995)."""
+    B, n, L, ck = 32, 256, 16, 4
+    lat = lbm.Lattice(n, n, B, tau=0.500375, force_amp=8e-5, force_mode=4, device=DEV)
+    ux = torch.tensor(inputs.noise((B, n, n), 5, 0.02), dtype=torch.float32, device=DEV)
+    uy = torch.tensor(inputs.noise((B, n, n), 6, 0.02), dtype=torch.float32, device=DEV)
+    lat.init_equilibrium(torch.ones((B, n, n), device=DEV), ux, uy)
+    f0 = lat.get_state()
+    theta0 = torch.tensor(inputs.xavier_mlp(3, out_scale=0.01), dtype=torch.float32, device=DEV)
+    ws = torch.empty(lat.record_bytes(L, ck) // 4, dtype=torch.float32, device=DEV)
+    grads = {}
+    for prec in ("f32", "bf16"):
+        w = lbm.weights_struct(theta0)
+        lat.set_state(f0)
+        lat.forward_record(L, ck, w, ws, prec)
+        _, g = lat.velocity_loss(ux, uy)
+        dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=DEV)
+        lat.backward(g, w, ws, dW, None, prec)
+        assert lat.status() == lbm.LBM_OK
+        grads[prec] = dW.double()
+
+    def loss_at(theta):
+        lat.set_state(f0)
+        lat.step(L, "mlp_f32", lbm.weights_struct(theta))
+        loss, _ = lat.velocity_loss(ux, uy)
+        return float(loss.item())
+
+    d = torch.randn(theta0.shape, generator=torch.Generator().manual_seed(4)).to(DEV)
+    d /= d.norm()
+    eps = 1e-2
+    fd = (loss_at(theta0 + eps * d) - loss_at(theta0 - eps * d)) / (2 * eps)
+    dd = float((grads["f32"] * d.double()).sum())
+    assert abs(fd - dd) <= 2e-3 * abs(dd), (fd, dd)
+    g32, gtc = grads["f32"], grads["bf16"]
+    rel = float((gtc - g32).norm() / g32.norm())
+    cos = float((gtc @ g32) / (gtc.norm() * g32.norm()))
+    print(f"full-size gradients: FD {fd:.6e} adjoint {dd:.6e}; tc vs f32 rel L2 {rel:.3e} cos {cos:.5f}")
+    assert rel <= 5e-2 and cos >= 0.995, (rel, cos)
