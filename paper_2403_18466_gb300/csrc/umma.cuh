@@ -215,25 +215,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2_alu(float lo, float hi) {
   asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(r) : "r"(a), "r"(b));
   return r;
 }
-// Hardware tanh approximation (FP32).
-__device__ __forceinline__ float tanh_f32(float x) {
-  float r;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-// tanh(a) and its derivative 1 - tanh(a)^2 to a few ulp, from t = e^{-2|a|}:
-// tanh a = sign(a) (1 - t) / (1 + t),  1 - tanh^2 a = 4 t / (1 + t)^2.
-// Two XU operations (ex2, rcp), the same XU cost as one tanh.approx.f32, but
-// the derivative keeps its relative accuracy for saturated units, where
-// 1 - h^2 formed from an approximate h would not.
-__device__ __forceinline__ void tanh_and_derivative(float a, float &h, float &dh) {
-  float t, r;
-  const float e = -2.8853900817779268f * fabsf(a);  // -2 log2(e) |a|
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(e));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
-  h = copysignf((1.0f - t) * r, a);
-  dh = 4.0f * t * r * r;
-}
 // Hardware tanh approximation on packed bf16x2.
 __device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
   uint32_t r;
