@@ -225,6 +225,9 @@ struct TilePos {
   }
 };
 
+__device__ __forceinline__ void prefetch_l2(const float *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -458,6 +461,26 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int ys = cy(i) == 0 ? T.y : (cy(i) == 1 ? ym : yp);
           d[i] = __ldg(gb + (size_t)i * plane + ys * nx + xs);
           pb[i] = __ldg(lb + (size_t)i * plane);
+        }
+      }
+      // ---- the next tile's inputs are prefetched into the L2 cache now, so
+      // that its loads return from L2 (no registers are held for them)
+      if (it + 1 < count) {
+        TilePos N = T;
+        N.advance(nx, ny);
+        const int xn = N.x0 + r;
+        if (xn < nx) {
+          const int nym = N.y == 0 ? ny - 1 : N.y - 1, nyp = N.y == ny - 1 ? 0 : N.y + 1;
+          const int nxm = xn == 0 ? nx - 1 : xn - 1, nxp = xn >= nx - 1 ? 0 : xn + 1;
+          const float *gb = state + (size_t)N.b * Q * plane;
+          const float *lb = lam_next + (size_t)N.b * Q * plane + N.y * nx + xn;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const int xs = cx(i) == 0 ? xn : (cx(i) == 1 ? nxm : nxp);
+            const int ys = cy(i) == 0 ? N.y : (cy(i) == 1 ? nym : nyp);
+            prefetch_l2(gb + (size_t)i * plane + ys * nx + xs);
+            prefetch_l2(lb + (size_t)i * plane);
+          }
         }
       }
       // ---- forward recompute: moments, equilibrium, layer-1 operand
