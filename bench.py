@@ -159,6 +159,22 @@ def _time_steps(lat, kind, w, steps, torch, stream):
     return start.elapsed_time(end)  # ms
 
 
+def _time_steps_segments(lat, kind, w, steps, torch, stream, nseg=5):
+    """The same timed region as _time_steps, issued as nseg back-to-back
+    segments with an event between them (events do not stall the stream).
+    Returns the whole region's ms and the per-step ms of each segment."""
+    nseg = max(1, min(nseg, steps))
+    sizes = [steps // nseg + (1 if i < steps % nseg else 0) for i in range(nseg)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nseg + 1)]
+    ev[0].record(stream)
+    for i, k in enumerate(sizes):
+        lat.step(k, kind, w)
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) / k for i, k in enumerate(sizes)]
+    return ev[0].elapsed_time(ev[-1]), per_step
+
+
 def run_gpu(args):
     import torch
     from paper_2403_18466_gb300 import inputs, lbm
@@ -187,7 +203,7 @@ def run_gpu(args):
     _barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(gpu_id) as clk:
-        ms = _time_steps(lat, "mlp_bf16", w, args.steps, torch, stream)
+        ms, seg = _time_steps_segments(lat, "mlp_bf16", w, args.steps, torch, stream)
     torch.cuda.synchronize()
     _barrier(world)
     ms_max = _max_over_ranks(ms, world, dev)
@@ -255,6 +271,9 @@ def run_gpu(args):
                    "parallelism": f"replicas{world}"},
         "roofline": roofline, "binding_unit": binding, "clocks": clocks, "e2e": e2e,
         "gpu_launches": args.steps, "components": comps, "status": lbm.lbm_strerror(status),
+        "segments": {"n": len(seg), "ms_per_step_median": round(statistics.median(seg), 5),
+                     "ms_per_step_best": round(min(seg), 5),
+                     "ms_per_step_worst": round(max(seg), 5)},
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
