@@ -87,7 +87,7 @@ cudaError_t launch_reduce_dw(const float *dw_partials, int rows, float *dW, cuda
 
 // adjoint_tc.cu ----------------------------------------------------------------
 // Tensor-core adjoint step (BF16 operands, FP32 accumulation); one partial row
-// per warpgroup.
+// per CTA (one persistent CTA per SM).
 int adjoint_tc_rows(const Grid &g, int sms);
 cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *lam_next,
                               float *lam_out, const CollideParams &p, const MlpF32 &w,
