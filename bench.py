@@ -453,10 +453,38 @@ def cpu_baseline(seconds=12.0, n=1024):
     oracle.run(oracle.MLP, g, k, prm, theta)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(n * n * k / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
-            "kind": "oracle",
-            "sample": f"FP64 oracle, learned collision, {n}x{n} crop of the same recipe, "
-                      f"{k} steps, {dt:.1f} s"}
+    out = {"value": round(n * n * k / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
+           "kind": "oracle",
+           "sample": f"FP64 oracle, learned collision, {n}x{n} crop of the same recipe, "
+                     f"{k} steps, {dt:.1f} s"}
+    # the other collisions on all cores, and the learned one on a single core
+    # (a child process, so that its OpenMP runtime starts with one thread)
+    comps = {}
+    for name, kind in (("bgk", oracle.BGK), ("smag", oracle.SMAG)):
+        prm_k = oracle.params(TAU, smag_cs=0.1 if kind == oracle.SMAG else 0.0,
+                              force_amp=FORCE_AMP, force_mode=FORCE_MODE)
+        t0 = time.perf_counter()
+        oracle.run(kind, g, 20, prm_k)
+        t = time.perf_counter() - t0
+        comps[f"{name}_{n}^2_20_steps"] = {"mlups": round(n * n * 20 / t / 1e6, 3),
+                                           "cores": cores}
+    code = ("import time, oracle; from paper_2403_18466_gb300 import inputs; import bench;"
+            "r, u, v = inputs.random_velocity_field(256, 256, seed=2, k0=0.5, urms=0.02);"
+            "g = oracle.stream_push(oracle.equilibrium_field(r[None], u[None], v[None]));"
+            "p = oracle.params(bench.TAU, force_amp=bench.FORCE_AMP, force_mode=bench.FORCE_MODE);"
+            "th = inputs.xavier_mlp(3, out_scale=bench.OUT_SCALE);"
+            "t0 = time.perf_counter(); oracle.run(oracle.MLP, g, 5, p, th);"
+            "print(256 * 256 * 5 / (time.perf_counter() - t0) / 1e6)")
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env,
+                             capture_output=True, text=True, timeout=120)
+        comps["mlp_256^2_5_steps_1_core"] = {"mlups": round(float(res.stdout.strip().splitlines()[-1]), 3),
+                                             "cores": 1}
+    except Exception as e:  # the single-core figure is informative only
+        comps["mlp_256^2_5_steps_1_core"] = {"unavailable": str(e)[:200]}
+    out["components"] = comps
+    return out
 
 
 def run_reference(args):
