@@ -59,7 +59,10 @@ typedef enum {
 } lbm_collision;
 
 typedef struct {
-  int nx, ny, batch;   /* grid and number of independent lattices (>= 1 each) */
+  int nx, ny, batch;   /* grid and number of independent lattices (>= 1 each;
+                          ny, batch <= 65535; nx*ny <= 2^31 - 1;
+                          ceil(nx/128)*ny*batch <= 2^31 - 1; 9*nx*ny*batch <= 2^40;
+                          lbm_init returns LBM_ERR_ARG beyond these) */
   double tau;          /* relaxation time, > 0.5 (Eq. S3, S6) */
   double smag_cs;      /* Smagorinsky constant C_s (used by LBM_SMAG) */
   double smag_delta;   /* filter width Delta in lattice units (LBM_SMAG) */
@@ -277,6 +280,8 @@ int lbm_run_host(lbm_ctx *ctx, const float *f_pre_host, int n, lbm_collision kin
  * earlier call needs clearing -- but calls that overlap on the GPU (for
  * example on two streams at once) race on the array and must be serialised by
  * the caller.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * ny and batch must not exceed 65535 (they index the launch grid), else
+ * LBM_ERR_ARG.
  * Returns LBM_OK, LBM_ERR_ARG (null pointer, size <= 0, or beyond the limit),
  * LBM_ERR_UNSUPPORTED (device ordinal >= 256) or LBM_ERR_CUDA. */
 int lbm_velocity_loss_noalloc(const float *state, int nx, int ny, int batch, const float *utx,

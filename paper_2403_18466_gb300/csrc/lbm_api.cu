@@ -50,9 +50,16 @@ namespace {
     if (e_ != cudaSuccess) return LBM_ERR_CUDA; \
   } while (0)
 
+// Largest lattice every kernel can address: the node-per-thread kernels put
+// ny and batch in gridDim.y and gridDim.z (at most 65535 each); the tiled
+// tensor-core kernels count nodes of one plane (nx*ny) and 128-node tiles
+// (ceil(nx/128)*ny*batch) in 32-bit integers; element offsets are 64-bit.
 bool bad_params(const lbm_params *p) {
   if (!p) return true;
   if (p->nx < 1 || p->ny < 1 || p->batch < 1) return true;
+  if (p->ny > 65535 || p->batch > 65535) return true;
+  if ((long long)p->nx * p->ny > 0x7FFFFFFFLL) return true;
+  if (((long long)p->nx + 127) / 128 * p->ny * p->batch > 0x7FFFFFFFLL) return true;
   if ((long long)p->nx * p->ny * p->batch * 9 > (1LL << 40)) return true;
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return true;
   if (!(p->smag_cs >= 0.0) || !(p->smag_delta > 0.0)) return true;

@@ -50,6 +50,7 @@ extern "C" int lbm_velocity_loss_noalloc(const float *state, int nx, int ny, int
                                          const float *utx, const float *uty, float *loss,
                                          float *dL_df, void *cuda_stream) {
   if (!state || !utx || !uty || !loss || nx < 1 || ny < 1 || batch < 1) return LBM_ERR_ARG;
+  if (ny > 65535 || batch > 65535) return LBM_ERR_ARG;  // gridDim.y / gridDim.z of the launch
   const long long partials = ((long long)nx + 127) / 128 * ny * batch;
   if (partials > kMaxPartials) return LBM_ERR_ARG;  // beyond the fixed scratch array
   float *scratch = nullptr;

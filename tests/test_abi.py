@@ -54,6 +54,34 @@ def test_host_side_argument_errors(lib):
     lib.lbm_destroy(None)
 
 
+@pytest.mark.parametrize("nx,ny,batch", [
+    (8, 65536, 1),          # ny beyond gridDim.y of the node-per-thread kernels
+    (8, 8, 65536),          # batch beyond gridDim.z
+    (46341, 46341, 1),      # nx*ny beyond a 32-bit plane index (~155 GB per buffer pair)
+    (2 ** 31 - 1, 2, 1),    # nx*ny just past 2^31 - 1
+    (128, 65535, 65535),    # 128-node tile count beyond 2^31 - 1 (and 9*nodes > 2^40)
+])
+def test_init_rejects_sizes_no_kernel_can_address(lib, nx, ny, batch):
+    """Sizes the kernels cannot index are refused on the host before any CUDA
+    call (fake, never-dereferenced buffer addresses)."""
+    from paper_2403_18466_gb300 import lbm
+    ctx = C.c_void_p()
+    p = lbm.make_params(nx, ny, batch, tau=0.6)
+    assert lib.lbm_init(C.byref(ctx), C.byref(p), C.c_void_p(256), C.c_void_p(512), None) \
+        == lbm.LBM_ERR_ARG
+    assert not ctx.value
+
+
+def test_noalloc_loss_rejects_grid_beyond_launch_limits(lib):
+    """ny or batch beyond 65535 would exceed the launch grid: LBM_ERR_ARG on the
+    host, before the scratch address is looked up (fake device pointers)."""
+    from paper_2403_18466_gb300 import lbm
+    fake = C.c_void_p(256)
+    for nx, ny, batch in ((1, 100000, 1), (1, 1, 70000)):
+        assert lib.lbm_velocity_loss_noalloc(fake, nx, ny, batch, fake, fake, fake, None,
+                                             None) == lbm.LBM_ERR_ARG
+
+
 def test_record_bytes_and_strerror(lib):
     from paper_2403_18466_gb300 import lbm
     p = lbm.make_params(256, 256, 32, tau=0.500375)
