@@ -134,6 +134,38 @@ float *lbm_state_buffer(lbm_ctx *ctx);
 int lbm_status(lbm_ctx *ctx);
 int lbm_clear_status(lbm_ctx *ctx);
 
+/* Failure detection (no counterpart in the paper): the tensor-core step
+ * kernel waits for each of its GEMMs with a bounded number of mbarrier polls
+ * and, when a wait runs out, stops, frees its tensor memory and sets the
+ * status that lbm_status reports as LBM_ERR_TIMEOUT (the state written by
+ * that step is then incomplete).  This sets the number of polls per wait for
+ * the later lbm_step calls of this context; 0 restores the default (2^20,
+ * far above any real GEMM latency).  A small value lets a test make a wait
+ * run out on purpose; the kernel's final wait for its own outstanding GEMM
+ * always uses the default, so tensor memory is never released under a GEMM
+ * in flight.  Host-side only; LBM_ERR_ARG for a NULL context. */
+int lbm_set_wait_limit(lbm_ctx *ctx, unsigned polls);
+
+/* The hidden-layer activation of LBM_MLP_BF16 (tanh, Eq. S10 network) applied
+ * element-wise, for checking its accuracy: out[k] = act(a[k]) for n FP32
+ * pre-activations a (device arrays, caller-owned, asynchronous on
+ * cuda_stream).  The tensor-core step evaluates some hidden units on the XU
+ * and the others on the FMA pipe:
+ *   path 0: the XU form, bf16 rounding then tanh.approx.bf16x2 (a bf16 value);
+ *   path 1: the FMA form as the step stores it, y P(min(y^2, 1)) with
+ *           y = a/4 and a degree-8 polynomial P, rounded to bf16 and clamped
+ *           to [-1, 1] (a bf16 value);
+ *   path 2: the FMA form before its bf16 rounding (FP32, clamped to [-1, 1]).
+ * LBM_ERR_ARG for a NULL pointer, n < 0 or another path. */
+int lbm_activation(const float *a, int n, int path, float *out, void *cuda_stream);
+
+/* Compiled layout of the LBM_MLP_BF16 step kernel (no counterpart in the
+ * paper; for performance accounting): *warpgroups_per_sm tiles of 128 nodes in
+ * flight per SM, and *xu_pairs_per_8 -- of every 8 pairs of hidden units, how
+ * many the XU evaluates (path 0 of lbm_activation; the rest use path 1).
+ * Either pointer may be NULL.  Host-only, no GPU needed; returns LBM_OK. */
+int lbm_mlp_bf16_layout(int *warpgroups_per_sm, int *xu_pairs_per_8);
+
 /* Velocity loss of the current state against targets (utx, uty) [b][y][x]:
  * L = 1/(2 N B) sum |u - u_t|^2 with u = j/rho of the pre-collision
  * populations (velocity form of Eq. S13), written to loss[0] (device,

@@ -164,13 +164,6 @@ __device__ __forceinline__ void mma_ta(uint32_t d, uint32_t a_tmem, uint64_t b, 
       "r"(a_tmem), "l"(b), "r"(id), "r"(acc ? 1u : 0u)
       : "memory");
 }
-// 8 consecutive columns of this thread's lane (the x8 form of tmem_st16).
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-      : "memory");
-}
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) { return pack_bf16x2(lo, hi); }
 __device__ __forceinline__ float lrelu(float v) { return fmaxf(v, LEAKY * v); }
 

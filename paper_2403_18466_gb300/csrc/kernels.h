@@ -72,9 +72,19 @@ cudaError_t launch_step_mlp_f32(const Grid &g, const float *in, float *out,
 
 // mlp_bf16.cu ------------------------------------------------------------------
 // weights: FP32 (dtype 0) or BF16 (dtype 1), same packed row-major layout.
+// wait_limit: polls of each bounded mbarrier wait before the kernel gives up
+// and sets *timeout_flag (0 = the default, 2^20).
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wptr[6], int dtype,
-                                 int *flag, int *timeout_flag, cudaStream_t s);
+                                 int *flag, int *timeout_flag, cudaStream_t s,
+                                 unsigned wait_limit = 0);
+
+// Compiled layout of the tensor-core step: tile warpgroups per SM and, of
+// every 8 activation pairs, how many the XU evaluates.
+void mlp_bf16_layout(int *warpgroups, int *xu_pairs_per_8);
+// The step kernel's activations element-wise (0: XU path, 1: FMA path as
+// stored, 2: FMA path before its bf16 rounding).
+cudaError_t launch_activation(const float *a, int n, int path, float *out, cudaStream_t s);
 
 // adjoint.cu -------------------------------------------------------------------
 // Number of CTAs (= rows of per-CTA dW partials) of the adjoint step.

@@ -42,6 +42,7 @@ struct Moments {
   float drho;  // rho - 1
   float rho;
   float ux, uy;
+  float inv_rho;  // 1/rho, rounded to nearest
 };
 
 __device__ __forceinline__ Moments node_moments(const float d[Q]) {
@@ -51,6 +52,7 @@ __device__ __forceinline__ Moments node_moments(const float d[Q]) {
   const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
   m.rho = 1.0f + m.drho;
   const float inv = 1.0f / m.rho;
+  m.inv_rho = inv;
   m.ux = jx * inv;
   m.uy = jy * inv;
   return m;
@@ -69,9 +71,10 @@ __device__ __forceinline__ void shifted_feq(const Moments &m, float deq[Q]) {
 // EDM forcing term f_ext_i = feq_i(rho, u + F/rho) - feq_i(rho, u)  (Eq. S5)
 // for F = (fx, 0), written without the cancellation of two equilibria:
 // with a = F/rho, (c.u_s)^2 - (c.u)^2 = (c.a)(c.(2u + a)) and
-// |u_s|^2 - |u|^2 = a.(2u + a); rho a = F.
+// |u_s|^2 - |u|^2 = a.(2u + a); rho a = F.  a = F (1/rho) with the rounded
+// reciprocal of the moments, so no kernel divides here.
 __device__ __forceinline__ void add_edm_force_x(const Moments &m, float fx, float out[Q]) {
-  const float ax = fx / m.rho;
+  const float ax = fx * m.inv_rho;
   const float sx = 2.0f * m.ux + ax;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {

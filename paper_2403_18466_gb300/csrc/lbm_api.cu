@@ -36,6 +36,7 @@ struct lbm_ctx {
   double *d_diag_part;  // partial sums
   size_t diag_part_cap;
   void *fft_plan;
+  unsigned wait_limit;  // polls per bounded device wait of the tensor-core kernels (0: default)
   // last lbm_forward_record
   int rec_n, rec_k;
   const void *rec_ws;
@@ -97,7 +98,7 @@ cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind
     case LBM_MLP_BF16: {
       const void *wp[6] = {w->w1, w->b1, w->w2, w->b2, w->w3, w->b3};
       return lbm::launch_step_mlp_bf16(c->g, in, out, c->cp, wp, w->dtype, c->d_flag,
-                                       c->d_flag + 1, c->stream);
+                                       c->d_flag + 1, c->stream, c->wait_limit);
     }
   }
   return cudaErrorInvalidValue;
@@ -272,6 +273,23 @@ int lbm_status(lbm_ctx *c) {
 int lbm_clear_status(lbm_ctx *c) {
   if (!c) return LBM_ERR_ARG;
   CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, 3 * sizeof(int), c->stream));
+  return LBM_OK;
+}
+
+int lbm_mlp_bf16_layout(int *warpgroups_per_sm, int *xu_pairs_per_8) {
+  lbm::mlp_bf16_layout(warpgroups_per_sm, xu_pairs_per_8);
+  return LBM_OK;
+}
+
+int lbm_activation(const float *a, int n, int path, float *out, void *cuda_stream) {
+  if (!a || !out || n < 0 || path < 0 || path > 2) return LBM_ERR_ARG;
+  CUDA_TRY(lbm::launch_activation(a, n, path, out, static_cast<cudaStream_t>(cuda_stream)));
+  return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_ctx *c, unsigned polls) {
+  if (!c) return LBM_ERR_ARG;
+  c->wait_limit = polls;
   return LBM_OK;
 }
 

@@ -7,44 +7,49 @@
 //   x = (f - feq)/rho;  h1 = tanh(W1 x + b1);  h2 = tanh(W2 h1 + b2);  o = W3 h2 + b3
 //   f' = f + (feq - f)/tau + (rho/tau) P o + f_ext,   P = mass/momentum projection
 //
-// Work decomposition.  A tile is 128 consecutive nodes of one row; one
-// warpgroup (128 threads, thread r = node r = tensor-memory lane r) owns a
-// tile at a time, and a CTA holds WGS warpgroups; every warpgroup walks its
-// own contiguous range of tiles (persistent, grid = CTAS_PER_SM CTAs per SM).  Each layer is one GEMM with
-// M = 128 nodes:
+// Work decomposition.  A tile is 128 consecutive nodes of one row; a
+// warpgroup (128 threads, thread r = node r = tensor-memory lane r) owns one
+// tile at a time and walks its own contiguous range of tiles; one persistent
+// CTA per SM holds WGS warpgroups.  Each layer is one GEMM with M = 128 nodes
+// and BOTH activation operands in tensor memory (tcgen05.mma with A in TMEM):
 //   layer 1: [128 x 16] x [16 x 64]   K = 9 inputs + a constant-1 column (b1) + 6 zeros
-//   layer 2: [128 x 80] x [80 x 64]   K = 64 hidden + constant-1 column (b2) + 15 zeros
-//   layer 3: [128 x 80] x [80 x 16]   N = 9 outputs + 7 zero columns, b3 via the 1-column
-// so the biases ride on the MMA.  Operands live in shared memory in the
-// canonical K-major no-swizzle layout (umma.cuh); the accumulators of all
-// three layers share the warpgroup's 64 tensor-memory columns (each layer's
-// accumulator has been read back before the next GEMM is issued).  Between
-// layers each thread reads its own row back with tcgen05.ld, rounds pairs to
-// bf16x2 and applies the hardware tanh on the packed pairs, and writes the
-// next operand row.  The populations of the next tile are loaded while the
-// current tile's GEMMs run, and its layer-1 operand is written while the
-// third GEMM runs (layer 1 has read its operand by then).
+//   layer 2: [128 x 64] x [64 x 64]   + [128 x 16 ones-column] x [16 x 64 (b2 | 0)]
+//   layer 3: [128 x 64] x [64 x 16]   + the same ones-column x [16 x 16 (b3 | 0)]
+// The per-tile tensor memory is the accumulator (64 columns) and the bf16 A
+// operand (64 values = 32 columns): 96 columns, 5 tiles per SM plus one shared
+// 8-column block whose first K element is 1 in every lane (the A operand of
+// the bias MMAs).  Only the weights (14.5 KB per tile) are read from shared
+// memory by the tensor core, so the GEMMs do not compete with anything else
+// for the SM's shared-memory bandwidth.
 //
-// Binding unit: the XU (MUFU) pipe.  Measured on this GPU with the
-// epilogue's instruction mix (cvt + tanh.approx.bf16x2 per pair), the XU
-// sustains ~0.24 tanh warp instructions per cycle per SM when 16 warps per SM
-// feed it, so the 128 activations of a node cap the step near 37 G nodes/s
-// however the GEMMs and memory traffic are scheduled (HBM alone would allow
-// 94 G); with fewer warps in their tanh phase at once it reaches less.  Hence
-// one CTA per SM of eight warpgroups (32 warps, 64 registers per thread; all
-// 512 tensor-memory columns, 207 KB of shared memory): more warpgroups per SM
-// keep more of them in their tanh epilogues at any time (measured at 4096^2:
-// 4 warpgroups per SM 19.8 G nodes/s, 6: 23.6 G, 8: 24.3 G).  The tanh
-// epilogue works through 16 columns at a time to stay within that register
-// budget.
+// Between layers each thread reads its accumulator row with tcgen05.ld,
+// applies tanh and writes the bf16 row back as the next A operand with
+// tcgen05.st.  The activations are split between two units (TANH_XU_PAIRS of
+// every 8 pairs on the XU, the rest on the FMA pipe), because the XU alone
+// caps the step near 40 G nodes/s:
+//   XU pairs:  cvt.rn.bf16x2.f32, then tanh.approx.bf16x2;
+//   FMA pairs: the hidden units' weight rows and biases are pre-scaled by 1/4
+//     (exact in bf16), so the accumulator holds y = a/4;  u = min(y^2, 1)
+//     (fma.sat), tanh(a) ~ y P(u) with the degree-8 relative minimax
+//     polynomial P of tanh(4 sqrt(u))/sqrt(u) on [0, 1] (odd in y, so small
+//     activations keep their relative accuracy) in packed fma.rn.f32x2,
+//     rounded to bf16 (cvt.rn) and clamped to [-1, 1] (min.xorsign.abs).
+//     Maximum error before the rounding: 0.36 bf16 ulp of tanh (half-ulp bar
+//     checked in float32 and on the GPU against tanhf); |a| >= 4 gives +-1,
+//     which is the bf16 rounding of tanh(a) there.
 //
-// Synchronisation per warpgroup: operand rows written by all 128 threads
-// -> fence.proxy.async + named barrier -> one thread issues the MMAs and
-// commits them to the warpgroup's mbarrier -> that thread alone polls the
-// mbarrier (bounded) while the others sleep in a named barrier that also
-// carries its verdict (bar.red.or), so a time-out is seen by the whole
-// warpgroup at once: it leaves the loop, the leader sets the timeout flag and
-// drains its outstanding commit, and tensor memory is freed.
+// Per node the moments, equilibrium, x and the BGK + force update are
+// computed once, while the previous tile's last GEMM runs; the epilogue of
+// layer 3 only projects o and adds (rho/tau) P o to the stored update.
+//
+// Synchronisation per warpgroup: tensor-memory stores of all 128 threads ->
+// tcgen05.wait::st + fence::before_thread_sync + named barrier -> one thread
+// issues the MMAs and commits them to the warpgroup's mbarrier -> that thread
+// alone polls the mbarrier (bounded) while the others sleep in a named
+// barrier that also carries its verdict (bar.red.or), so a time-out is seen by
+// the whole warpgroup at once: it leaves the loop, the leader sets the timeout
+// flag and drains its outstanding commit (full limit), and tensor memory is
+// always freed.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -58,44 +63,72 @@ using namespace umma;
 
 constexpr int WG_THREADS = 128;
 #ifndef LBM_BF16_WGS
-#define LBM_BF16_WGS 8
+#define LBM_BF16_WGS 5
 #endif
-#ifndef LBM_BF16_CTAS_PER_SM
-#define LBM_BF16_CTAS_PER_SM 1
+#ifndef LBM_TANH_XU_PAIRS
+#define LBM_TANH_XU_PAIRS 5
 #endif
-constexpr int WGS = LBM_BF16_WGS;                  // warpgroups per CTA
-constexpr int CTAS_PER_SM = LBM_BF16_CTAS_PER_SM;  // resident CTAs per SM
+#ifndef LBM_TANH_XU_FORM
+#define LBM_TANH_XU_FORM 0
+#endif
+#ifndef LBM_TANH_FMA_PACK
+#define LBM_TANH_FMA_PACK 0
+#endif
+constexpr int WGS = LBM_BF16_WGS;  // tile warpgroups per CTA (one CTA per SM)
+// XU form: 0 = cvt.rn.bf16x2.f32 then tanh.approx.bf16x2 (20 XU cycles per
+// warp-wide pair); 1 = tanh.approx.f32 on both FP32 values, packed to bf16 on
+// the ALU (16 XU cycles per pair)
+constexpr int XU_FORM = LBM_TANH_XU_FORM;
+// bf16 packing of the FMA form: 0 = cvt.rn.bf16x2.f32 (XU), 1 = integer
+// rounding on the ALU (ties away from zero)
+constexpr int FMA_PACK = LBM_TANH_FMA_PACK;
 constexpr int THREADS = WGS * WG_THREADS;
-constexpr int K1 = 16, K2 = 80;        // padded K of layer 1 and of layers 2/3
-// per CTA: 64 columns per warpgroup, rounded up to a power of two >= 32
-constexpr uint32_t TMEM_COLS = WGS * 64 <= 64 ? 64 : (WGS * 64 <= 128 ? 128 : (WGS * 64 <= 256 ? 256 : 512));
-#ifndef LBM_BF16_SLEEP_NS
-#define LBM_BF16_SLEEP_NS 0
-#endif
-constexpr uint32_t WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
-constexpr uint32_t SLEEP_NS = LBM_BF16_SLEEP_NS;  // suspend hint per poll (0: plain polls)
+constexpr int XU_PAIRS = LBM_TANH_XU_PAIRS;  // of every 8 activation pairs, on the XU
+static_assert(XU_PAIRS >= 0 && XU_PAIRS <= 8, "split of 8 pairs");
+constexpr int K1 = 16, KH = 64, KB = 16;  // K of layer 1, of the hidden GEMMs, of the bias MMAs
+// tensor memory: per warpgroup the accumulator [0, 64) and the A operand
+// [64, 96); the shared ones-column block after the last warpgroup
+constexpr uint32_t WG_COLS = 96, C_ACC = 0, C_A = 64, C_ONE = WGS * WG_COLS;
+constexpr uint32_t TMEM_COLS = 512;
+static_assert(C_ONE + 8 <= TMEM_COLS, "tensor memory layout");
+constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
 
-__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase) {
-  if (SLEEP_NS == 0) return mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-  return mbar_wait_sleep_bounded(bar, phase, WAIT_LIMIT / 64, SLEEP_NS);
+// Bounded wait for a GEMM's commit.  A limit of 1024 polls or more uses
+// mbarrier.try_wait (the thread is suspended until the phase completes or a
+// short system time limit passes); a smaller limit polls with the
+// non-blocking test_wait, so that it runs out after that many polls -- the
+// way a test makes a wait give up.
+__device__ __forceinline__ bool wait_gemm(uint32_t bar, uint32_t phase, uint32_t limit) {
+  if (limit >= 1024) return mbar_wait_bounded(bar, phase, limit);
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_test_wait(bar, phase)) return true;
+  return false;
 }
 
+// Degree-8 relative minimax polynomial of tanh(4 sqrt(u)) / sqrt(u) on [0, 1]
+// (Lawson-weighted least squares, monomial basis, coefficients rounded to
+// float32); tanh(4y) ~ y P(y^2) for |y| <= 1.
+constexpr float TP0 = 3.9946699142456055f, TP1 = -20.35879898071289f, TP2 = 103.5002670288086f,
+                TP3 = -381.81884765625f, TP4 = 933.0108642578125f, TP5 = -1447.415283203125f,
+                TP6 = 1361.048095703125f, TP7 = -704.948486328125f, TP8 = 153.9882049560547f;
+
+// True if hidden unit n is evaluated on the FMA pipe (its pre-activation is
+// then accumulated pre-scaled by 1/4).
+__host__ __device__ constexpr bool fma_unit(int n) { return (n % 16) >= 2 * XU_PAIRS; }
+
 struct __align__(1024) Smem {
-  unsigned char w1[HIDDEN * K1 * 2];     // B of layer 1: [64 x 16]
-  unsigned char w2[HIDDEN * K2 * 2];     // B of layer 2: [64 x 80]
-  unsigned char w3[16 * K2 * 2];         // B of layer 3: [16 x 80]
-  unsigned char a1[WGS][128 * K1 * 2];   // A of layer 1, per warpgroup
-  unsigned char a23[WGS][128 * K2 * 2];  // A of layers 2 and 3, per warpgroup
+  unsigned char w1[HIDDEN * K1 * 2];  // B of layer 1: [64 x 16] = W1 | b1 | 0
+  unsigned char w2[HIDDEN * KH * 2];  // B of layer 2: [64 x 64] = W2
+  unsigned char w3[16 * KH * 2];      // B of layer 3: [16 x 64] = W3 | 0 rows
+  unsigned char bb2[HIDDEN * KB * 2]; // [64 x 16]: column 0 = b2
+  unsigned char bb3[16 * KB * 2];     // [16 x 16]: column 0 = b3
   unsigned long long bar[WGS];
   uint32_t taddr;
 };
-// Shared memory requested per CTA: padded so that no more than CTAS_PER_SM
-// CTAs share an SM (their tensor-memory allocations then always fit).
-constexpr size_t SMEM_NEED = sizeof(Smem) + 1024;
-constexpr size_t SMEM_FLOOR = (228 * 1024) / (CTAS_PER_SM + 1) + 1024;
-constexpr size_t SMEM_BYTES = SMEM_NEED > SMEM_FLOOR ? SMEM_NEED : SMEM_FLOOR;
-static_assert(SMEM_BYTES * CTAS_PER_SM <= 228 * 1024, "shared memory layout too large");
-static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory oversubscribed");
+// One CTA per SM (its tensor-memory allocation takes all 512 columns): the
+// dynamic shared memory request is padded so that no second CTA fits.
+constexpr size_t SMEM_BYTES = (sizeof(Smem) + 1024) > 120 * 1024 ? sizeof(Smem) + 1024 : 120 * 1024;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory layout too large");
 
 __device__ __forceinline__ void store_bf16(unsigned char *base, int r, int k, int K, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + canon_offset(r, k, K)) = __float2bfloat16_rn(v);
@@ -107,17 +140,74 @@ __device__ __forceinline__ float wload(const void *p, int i) {
   return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
 }
 
-__device__ __forceinline__ void project9(float o[Q]) {
-  float s = 0.f, sx = 0.f, sy = 0.f;
+// ---- activations ---------------------------------------------------------
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float sat_sq(float y) {
+  float u;
+  asm("fma.rn.sat.f32 %0, %1, %1, 0f00000000;" : "=f"(u) : "f"(y));
+  return u;
+}
+__device__ __forceinline__ uint32_t clamp_unit_bf16x2(uint32_t v) {
+  uint32_t r;
+  asm("min.xorsign.abs.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0x3F803F80u));
+  return r;
+}
+__device__ __forceinline__ float tanh_f32(float a) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+// XU pair: hardware tanh (see XU_FORM).
+__device__ __forceinline__ uint32_t act_xu(float a0, float a1) {
+  if (XU_FORM == 1) return pack_bf16x2_alu(tanh_f32(a0), tanh_f32(a1));
+  return tanh_bf16x2(pack_bf16x2(a0, a1));
+}
+// FMA pair: y0, y1 = a/4 of the two units; tanh(a) ~ y P(min(y^2, 1)).
+__device__ __forceinline__ uint32_t act_fma(float y0, float y1) {
+  const uint64_t u = f2(sat_sq(y0), sat_sq(y1));
+  uint64_t q = fma2(f2(TP8, TP8), u, f2(TP7, TP7));
+  q = fma2(q, u, f2(TP6, TP6));
+  q = fma2(q, u, f2(TP5, TP5));
+  q = fma2(q, u, f2(TP4, TP4));
+  q = fma2(q, u, f2(TP3, TP3));
+  q = fma2(q, u, f2(TP2, TP2));
+  q = fma2(q, u, f2(TP1, TP1));
+  q = fma2(q, u, f2(TP0, TP0));
+  const uint64_t h = mul2(f2(y0, y1), q);
+  const float h0 = __uint_as_float((uint32_t)h), h1 = __uint_as_float((uint32_t)(h >> 32));
+  return clamp_unit_bf16x2(FMA_PACK == 1 ? pack_bf16x2_alu(h0, h1) : pack_bf16x2(h0, h1));
+}
+
+// Accumulator columns [0, 64) of this thread's row -> tanh -> bf16 pairs in
+// A-operand columns [C_A, C_A + 32) of the same row.
+__device__ __forceinline__ void hidden_epilogue(uint32_t tm_row) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    s += o[i];
-    sx += (float)cx(i) * o[i];
-    sy += (float)cy(i) * o[i];
+  for (int c = 0; c < HIDDEN; c += 32) {
+    uint32_t v[32];
+    tmem_ld32(tm_row + C_ACC + c, v);
+    tmem_wait_ld();
+    uint32_t p[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float a0 = __uint_as_float(v[2 * q]), a1 = __uint_as_float(v[2 * q + 1]);
+      p[q] = fma_unit(c + 2 * q) ? act_fma(a0, a1) : act_xu(a0, a1);
+    }
+    tmem_st16(tm_row + C_A + c / 2, p);
   }
-  const float k1 = -s * (1.0f / 9.0f), k2 = -sx * (1.0f / 6.0f), k3 = -sy * (1.0f / 6.0f);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) o[i] += k1 + (float)cx(i) * k2 + (float)cy(i) * k3;
 }
 
 // Position of a tile: lattice b, row y, first column x0.  Walked incrementally.
@@ -135,79 +225,78 @@ struct TilePos {
   }
 };
 
-__device__ __forceinline__ void pull_node(const float *__restrict__ in, int plane, int nx,
+// Pre-collision populations (shifted) of node x of tile T: pull from the
+// upstream neighbours with periodic wrap.
+__device__ __forceinline__ void pull_node(const float *__restrict__ in, size_t plane, int nx,
                                           int ny, const TilePos &T, int x, float d[Q]) {
   const float *gb = in + (size_t)T.b * Q * plane;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
-  const int r0 = T.y * nx, rm = ym * nx, rp = yp * nx;
+  const size_t r0 = (size_t)T.y * nx, rm = (size_t)ym * nx, rp = (size_t)yp * nx;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int xs = cx(i) == 0 ? x : (cx(i) == 1 ? xm : xp);
-    const int rs = cy(i) == 0 ? r0 : (cy(i) == 1 ? rm : rp);
+    const size_t rs = cy(i) == 0 ? r0 : (cy(i) == 1 ? rm : rp);
     d[i] = __ldg(gb + (size_t)i * plane + rs + xs);
   }
 }
 
-// Read the 64 accumulator columns of this thread's row, tanh on packed bf16
-// pairs, write them as K columns 0..63 of the thread's layer-2/3 operand row.
-__device__ __forceinline__ void tanh_row_to_operand(uint32_t tm_row, unsigned char *a23, int r) {
-#pragma unroll
-  for (int c = 0; c < HIDDEN; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(tm_row + c, v);
-    tmem_wait_ld();
-    uint32_t p[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      p[q] = tanh_bf16x2(pack_bf16x2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])));
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8 * q, K2)) =
-          make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
-  }
-}
-
-// Moments of shifted populations, reciprocal of rho rounded to nearest: the
-// same arithmetic wherever a tile's moments are needed.
-__device__ __forceinline__ Moments moments_rn(const float d[Q], float &inv_rho) {
-  Moments m;
-  m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-  const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-  const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-  m.rho = 1.0f + m.drho;
-  inv_rho = __frcp_rn(m.rho);
-  m.ux = jx * inv_rho;
-  m.uy = jy * inv_rho;
-  return m;
-}
-
-// x = (f - feq)/rho of this thread's node -> row r of the layer-1 operand (9
-// inputs, the constant-1 bias column, zeros); flags an unstable node.
-__device__ __forceinline__ void prep_x(const float d[Q], bool active, unsigned char *a1, int r,
-                                       int *flag) {
-  float inv_rho;
-  const Moments m = moments_rn(d, inv_rho);
-  flag_unstable(active && is_unstable(m), flag);
+// Everything of a node's update that does not need the network: moments,
+// x = (f - feq)/rho as the layer-1 operand row (9 inputs, the constant-1 bias
+// column, zeros; bf16 with integer rounding on the ALU), the BGK + force
+// update (the same helpers as the BGK kernel, so a zero output layer
+// reproduces BGK bit for bit) and rho/tau.
+struct NodePrep {
+  uint32_t xp[8];
+  float base[Q];
+  float rw;
+  bool bad;
+};
+__device__ __forceinline__ void prep_node(const float d[Q], float omega, const float *force,
+                                          float fx, NodePrep &P) {
+  const Moments m = node_moments(d);
+  P.bad = is_unstable(m);
+  float deq[Q];
+  shifted_feq(m, deq);
   float xin[Q];
-  {
-    float deq[Q];
-    shifted_feq(m, deq);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+  for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * m.inv_rho;
+  P.xp[0] = pack_bf16x2_alu(xin[0], xin[1]);
+  P.xp[1] = pack_bf16x2_alu(xin[2], xin[3]);
+  P.xp[2] = pack_bf16x2_alu(xin[4], xin[5]);
+  P.xp[3] = pack_bf16x2_alu(xin[6], xin[7]);
+  P.xp[4] = pack_bf16x2_alu(xin[8], 1.0f);
+  P.xp[5] = P.xp[6] = P.xp[7] = 0u;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) P.base[i] = fmaf(omega, deq[i] - d[i], d[i]);
+  if (force) add_edm_force_x(m, fx, P.base);
+  P.rw = m.rho * omega;
+}
+
+// f' = base + (rho/tau) P o, with P the projection removing span{1, c_x, c_y}
+// (Eqs. S11-S12: kappa_1 = -sum o / 9, kappa_a = -sum o c_a / 6 for D2Q9).
+__device__ __forceinline__ void finish_node(const uint32_t ov[16], const NodePrep &P,
+                                            float out[Q]) {
+  float o[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
+  const float s = ((o[0] + o[1]) + (o[2] + o[3])) + ((o[4] + o[5]) + (o[6] + o[7])) + o[8];
+  const float sx = (o[1] - o[3]) + (o[5] - o[6]) + (o[8] - o[7]);
+  const float sy = (o[2] - o[4]) + (o[5] + o[6]) - (o[7] + o[8]);
+  const float k1 = -s * (1.0f / 9.0f), k2 = -sx * (1.0f / 6.0f), k3 = -sy * (1.0f / 6.0f);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float oi = o[i] + (k1 + ((float)cx(i) * k2 + (float)cy(i) * k3));
+    out[i] = fmaf(P.rw, oi, P.base[i]);
   }
-  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
-      make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
-                 pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
-  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
-      make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
 }
 
 template <int DTYPE>
-__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
+__global__ void __launch_bounds__(THREADS, 1)
     k_step_mlp_bf16(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
                     int batch, CollideParams p, const void *w1, const void *b1, const void *w2,
-                    const void *b2, const void *w3, const void *b3, int *flag, int *timeout_flag) {
+                    const void *b2, const void *w3, const void *b3, int *flag, int *timeout_flag,
+                    uint32_t wait_limit) {
   extern __shared__ unsigned char smem_raw[];
   Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                       ~uintptr_t(1023));
@@ -216,30 +305,33 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
   const int r = tid % WG_THREADS;   // row = node within the tile = TMEM lane
   const int warp_in_wg = r / 32;
 
-  // ---- prologue: weights -> bf16 operand tiles, constant columns, barriers, TMEM
+  // ---- prologue: weights -> bf16 operand tiles (FMA-path units pre-scaled
+  // by 1/4, exact in bf16), barriers, tensor memory, the ones-column block
   for (int e = tid; e < HIDDEN * K1; e += THREADS) {
     const int n = e / K1, k = e % K1;
-    const float v = k < 9 ? wload<DTYPE>(w1, n * 9 + k) : (k == 9 ? wload<DTYPE>(b1, n) : 0.f);
+    float v = k < 9 ? wload<DTYPE>(w1, n * 9 + k) : (k == 9 ? wload<DTYPE>(b1, n) : 0.f);
+    if (fma_unit(n)) v *= 0.25f;
     store_bf16(S.w1, n, k, K1, v);
   }
-  for (int e = tid; e < HIDDEN * K2; e += THREADS) {
-    const int n = e / K2, k = e % K2;
-    const float v =
-        k < HIDDEN ? wload<DTYPE>(w2, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b2, n) : 0.f);
-    store_bf16(S.w2, n, k, K2, v);
+  for (int e = tid; e < HIDDEN * KH; e += THREADS) {
+    const int n = e / KH, k = e % KH;
+    float v = wload<DTYPE>(w2, n * HIDDEN + k);
+    if (fma_unit(n)) v *= 0.25f;
+    store_bf16(S.w2, n, k, KH, v);
   }
-  for (int e = tid; e < 16 * K2; e += THREADS) {
-    const int n = e / K2, k = e % K2;
-    float v = 0.f;
-    if (n < 9)
-      v = k < HIDDEN ? wload<DTYPE>(w3, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b3, n) : 0.f);
-    store_bf16(S.w3, n, k, K2, v);
+  for (int e = tid; e < 16 * KH; e += THREADS) {
+    const int n = e / KH, k = e % KH;
+    store_bf16(S.w3, n, k, KH, n < 9 ? wload<DTYPE>(w3, n * HIDDEN + k) : 0.f);
   }
-  // constant K columns 64..79 of this thread's layer-2/3 operand row: 1, 0, ..., 0
-  {
-    unsigned char *a23 = S.a23[wg];
-    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = tid; e < HIDDEN * KB; e += THREADS) {
+    const int n = e / KB, k = e % KB;
+    float v = k == 0 ? wload<DTYPE>(b2, n) : 0.f;
+    if (fma_unit(n)) v *= 0.25f;
+    store_bf16(S.bb2, n, k, KB, v);
+  }
+  for (int e = tid; e < 16 * KB; e += THREADS) {
+    const int n = e / KB, k = e % KB;
+    store_bf16(S.bb3, n, k, KB, (k == 0 && n < 9) ? wload<DTYPE>(b3, n) : 0.f);
   }
   if (tid == 0) {
     for (int k = 0; k < WGS; ++k) mbar_init(smem_u32(&S.bar[k]), 1);
@@ -254,157 +346,210 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
   __syncthreads();
   fence_after_sync();
 
-  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 64);                // this WG's columns
-  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);  // + lane base
+  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * WG_COLS);               // this WG's columns
+  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);      // + lane base
+  if (wg == 0) {  // the ones-column block: K element 0 = 1 in every lane
+    const uint32_t one[8] = {0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    tmem_st8(S.taddr + C_ONE + ((uint32_t)(32 * warp_in_wg) << 16), one);
+    tmem_wait_st();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+
   const uint32_t bar = smem_u32(&S.bar[wg]);
   const uint32_t bar_id = 1 + wg;
   const bool leader = r == 0;
-  unsigned char *a1 = S.a1[wg];
-  unsigned char *a23 = S.a23[wg];
-  const uint64_t da1 = smem_desc(smem_u32(a1), 128, 16 * K1);
-  const uint64_t db1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
-  const uint32_t sa23 = smem_u32(a23), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
+  const uint32_t a_op = tm_wg + C_A, acc = tm_wg + C_ACC, ones = S.taddr + C_ONE;
+  const uint64_t dw1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
+  const uint64_t dbb2 = smem_desc(smem_u32(S.bb2), 128, 16 * KB);
+  const uint64_t dbb3 = smem_desc(smem_u32(S.bb3), 128, 16 * KB);
+  const uint32_t sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
   constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
 
   // ---- this warpgroup's contiguous range of tiles
-  const int plane = nx * ny;
+  const size_t plane = (size_t)nx * ny;
   const int tiles_x = (nx + WG_THREADS - 1) / WG_THREADS;
-  const int ntiles = tiles_x * ny * batch;
-  const int nwg = gridDim.x * WGS;
-  const int gwg = blockIdx.x * WGS + wg;
-  const int per = ntiles / nwg, extra = ntiles % nwg;
-  const int t_begin = gwg * per + min(gwg, extra);
-  const int count = per + (gwg < extra ? 1 : 0);
+  const long long ntiles = (long long)tiles_x * ny * batch;
+  const long long nwg = (long long)gridDim.x * WGS;
+  const long long gwg = (long long)blockIdx.x * WGS + wg;
+  const long long per = ntiles / nwg, extra = ntiles % nwg;
+  const long long t_begin = gwg * per + (gwg < extra ? gwg : extra);
+  const int count = (int)(per + (gwg < extra ? 1 : 0));
   TilePos T;
-  T.x0 = (t_begin % tiles_x) * WG_THREADS;
-  T.y = (t_begin / tiles_x) % ny;
-  T.b = t_begin / (tiles_x * ny);
+  T.x0 = (int)(t_begin % tiles_x) * WG_THREADS;
+  T.y = (int)((t_begin / tiles_x) % ny);
+  T.b = (int)(t_begin / ((long long)tiles_x * ny));
   const float omega = p.omega;
 
   uint32_t phase = 0;
   bool fail = false;  // the leader's last bounded wait gave up (leader only)
+  bool bad = false;   // an unstable node was met (per thread)
 
-  float d[Q];
+  NodePrep P;
+  {
+    float d[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) d[i] = 0.f;
-  if (count > 0 && T.x0 + r < nx) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
-  if (count > 0) prep_x(d, T.x0 + r < nx, a1, r, flag);
+    for (int i = 0; i < Q; ++i) d[i] = 0.f;
+    const bool act = count > 0 && T.x0 + r < nx;
+    if (act) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
+    prep_node(d, omega, p.force, (count > 0 && p.force) ? __ldg(p.force + T.y) : 0.f, P);
+    bad = act && P.bad;
+    tmem_st8(tm_row + C_A, P.xp);
+    tmem_wait_st();
+  }
 
   for (int it = 0; it < count; ++it) {
     const int x = T.x0 + r;
     const bool active = x < nx;
 
-    // ---- the tile's layer-1 operand rows are written (before the loop, or
-    // during the previous tile's third GEMM)
-    fence_proxy_async();
+    // ---- layer 1 (its operand rows were written before the loop or at the
+    // end of the previous tile)
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
-      mma_bf16(tm_wg, da1, db1, ID64, 0);
+      mma_bf16_ta(acc, a_op, dw1, ID64, 0);
       mma_commit(bar);
     }
 
-    // ---- prefetch the next tile's populations while the GEMMs run
+    // ---- prefetch the next tile's populations and force while the GEMMs run
     TilePos N = T;
     N.advance(nx, ny);
+    const bool more = it + 1 < count;
+    const bool nact = more && N.x0 + r < nx;
     float dn[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) dn[i] = 0.f;
-    if (it + 1 < count && N.x0 + r < nx) pull_node(in, plane, nx, ny, N, N.x0 + r, dn);
+    if (nact) pull_node(in, plane, nx, ny, N, N.x0 + r, dn);
+    const float fxn = (more && p.force) ? __ldg(p.force + N.y) : 0.f;
 
-    // ---- layer 1 epilogue: h1 = tanh(D1) -> operand of layer 2
-    // (one thread polls the mbarrier; the others sleep in the named barrier)
-    if (leader) fail = !wait_mma(bar, phase);
+    // ---- layer 1 epilogue: h1 -> A operand; layer 2
+    if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     phase ^= 1;
     fence_after_sync();
-    tanh_row_to_operand(tm_row, a23, r);
-    fence_proxy_async();
+    hidden_epilogue(tm_row);
+    tmem_wait_st();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
-      for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
-                 smem_desc(sw2 + 256 * s, 128, 16 * K2), ID64, s > 0);
+      for (int s = 0; s < KH / 16; ++s)
+        mma_bf16_ta(acc, a_op + 8 * s, smem_desc(sw2 + 256 * s, 128, 16 * KH), ID64, s > 0);
+      mma_bf16_ta(acc, ones, dbb2, ID64, 1);
       mma_commit(bar);
     }
 
-    // ---- layer 2 epilogue: h2 = tanh(D2) -> operand of layer 3
-    if (leader) fail = !wait_mma(bar, phase);
+    // ---- layer 2 epilogue: h2 -> A operand; layer 3
+    if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     phase ^= 1;
     fence_after_sync();
-    tanh_row_to_operand(tm_row, a23, r);
-    fence_proxy_async();
+    hidden_epilogue(tm_row);
+    tmem_wait_st();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
-      for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
-                 smem_desc(sw3 + 256 * s, 128, 16 * K2), ID16, s > 0);
+      for (int s = 0; s < KH / 16; ++s)
+        mma_bf16_ta(acc, a_op + 8 * s, smem_desc(sw3 + 256 * s, 128, 16 * KH), ID16, s > 0);
+      mma_bf16_ta(acc, ones, dbb3, ID16, 1);
       mma_commit(bar);
     }
 
-    // ---- the next tile's layer-1 operand while layer 3 runs (layer 1 of this
-    // tile has completed, so a1 is free)
-    if (it + 1 < count) prep_x(dn, N.x0 + r < nx, a1, r, flag);
+    // ---- the next tile's per-node work while layer 3 runs
+    NodePrep Pn;
+    prep_node(dn, omega, p.force, fxn, Pn);
+    bad |= nact && Pn.bad;
 
-    // ---- layer 3 epilogue: projection, BGK + learned correction + force, store
-    if (leader) fail = !wait_mma(bar, phase);
+    // ---- layer 3 epilogue: projection, update, store; the next tile's x
+    if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
+    phase ^= 1;
+    fence_after_sync();
     {
-      phase ^= 1;
-      fence_after_sync();
       uint32_t ov[16];
-      tmem_ld16(tm_row, ov);
+      tmem_ld16(tm_row + C_ACC, ov);
       tmem_wait_ld();
-      float o[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) o[i] = __uint_as_float(ov[i]);
-      project9(o);
+      if (more) tmem_st8(tm_row + C_A, Pn.xp);  // layer 3 has read the A operand
       if (active) {
-        float inv_rho;
-        const Moments m = moments_rn(d, inv_rho);
-        float deq[Q];
-        shifted_feq(m, deq);
-        const float rw = m.rho * omega;
+        float f[Q];
+        finish_node(ov, P, f);
+        float *ob = out + (size_t)T.b * Q * plane + (size_t)T.y * nx + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = fmaf(omega, deq[i] - d[i], d[i]) + rw * o[i];
-        // EDM force (Eq. S5) for F = (fx, 0): the helper the BGK kernel uses,
-        // so that a zero output layer reproduces BGK bit for bit
-        if (p.force) add_edm_force_x(m, __ldg(p.force + T.y), d);
-        float *ob = out + (size_t)T.b * Q * plane + T.y * nx + x;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) ob[(size_t)i * plane] = d[i];
+        for (int i = 0; i < Q; ++i) ob[(size_t)i * plane] = f[i];
       }
+      tmem_wait_st();
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = dn[i];
+    P = Pn;
     T = N;
   }
 
   // the leader's wait gave up (the whole warpgroup left the loop together):
-  // flag it and drain the outstanding commit (bounded) before tensor memory
-  // is released
+  // flag it and drain the outstanding commit (full limit) before tensor
+  // memory is released
   if (leader && fail) {
     atomicOr(timeout_flag, 1);
-    wait_mma(bar, phase);
+    mbar_wait_bounded(bar, phase, DEFAULT_WAIT_LIMIT);
   }
+  flag_unstable(bad, flag);
   fence_before_sync();
   __syncthreads();
   if (tid < 32) tmem_dealloc(S.taddr, TMEM_COLS);
 }
 
+// The activations of the step kernel applied element-wise (path 0: XU pair,
+// 1: FMA pair as stored, 2: FMA pair before its bf16 rounding), for tests of
+// their accuracy against tanh.  Odd counts: the last pair repeats its input.
+__global__ void k_activation(const float *__restrict__ a, int n, int path, float *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * j >= n) return;
+  const float a0 = a[2 * j], a1 = 2 * j + 1 < n ? a[2 * j + 1] : a0;
+  float r0, r1;
+  if (path == 2) {
+    const float y0 = 0.25f * a0, y1 = 0.25f * a1;
+    const uint64_t u = f2(sat_sq(y0), sat_sq(y1));
+    uint64_t q = fma2(f2(TP8, TP8), u, f2(TP7, TP7));
+    q = fma2(q, u, f2(TP6, TP6));
+    q = fma2(q, u, f2(TP5, TP5));
+    q = fma2(q, u, f2(TP4, TP4));
+    q = fma2(q, u, f2(TP3, TP3));
+    q = fma2(q, u, f2(TP2, TP2));
+    q = fma2(q, u, f2(TP1, TP1));
+    q = fma2(q, u, f2(TP0, TP0));
+    const uint64_t h = mul2(f2(y0, y1), q);
+    r0 = fminf(fmaxf(__uint_as_float((uint32_t)h), -1.0f), 1.0f);
+    r1 = fminf(fmaxf(__uint_as_float((uint32_t)(h >> 32)), -1.0f), 1.0f);
+  } else {
+    const uint32_t v = path == 0 ? act_xu(a0, a1) : act_fma(0.25f * a0, 0.25f * a1);
+    r0 = __uint_as_float(v << 16);
+    r1 = __uint_as_float(v & 0xffff0000u);
+  }
+  out[2 * j] = r0;
+  if (2 * j + 1 < n) out[2 * j + 1] = r1;
+}
+
 }  // namespace
+
+void mlp_bf16_layout(int *warpgroups, int *xu_pairs_per_8) {
+  if (warpgroups) *warpgroups = WGS;
+  if (xu_pairs_per_8) *xu_pairs_per_8 = XU_PAIRS;
+}
+
+cudaError_t launch_activation(const float *a, int n, int path, float *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int pairs = (n + 1) / 2;
+  k_activation<<<(pairs + 255) / 256, 256, 0, s>>>(a, n, path, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wp[6], int dtype,
-                                 int *flag, int *timeout_flag, cudaStream_t s) {
+                                 int *flag, int *timeout_flag, cudaStream_t s,
+                                 unsigned wait_limit) {
   static int sms = 0;
   static bool attr_done[2] = {false, false};
   if (!sms) {
@@ -421,12 +566,12 @@ cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
     attr_done[dtype] = true;
   }
   const long long tiles = (long long)((g.nx + WG_THREADS - 1) / WG_THREADS) * g.ny * g.batch;
-  if ((long long)g.nx * g.ny * g.batch * Q >= (1LL << 31) || tiles >= (1LL << 31))
-    return cudaErrorInvalidValue;  // 32-bit index arithmetic inside the kernel
   long long ctas = (tiles + WGS - 1) / WGS;
-  if (ctas > (long long)CTAS_PER_SM * sms) ctas = (long long)CTAS_PER_SM * sms;
+  if (ctas > (long long)sms) ctas = sms;
+  if (wait_limit == 0) wait_limit = DEFAULT_WAIT_LIMIT;
   kern<<<(unsigned)ctas, THREADS, SMEM_BYTES, s>>>(in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1],
-                                                   wp[2], wp[3], wp[4], wp[5], flag, timeout_flag);
+                                                   wp[2], wp[3], wp[4], wp[5], flag, timeout_flag,
+                                                   wait_limit);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ _SIGS = {
     "lbm_state_buffer": (_vp, [_vp]),
     "lbm_status": (_i, [_vp]),
     "lbm_clear_status": (_i, [_vp]),
+    "lbm_set_wait_limit": (_i, [_vp, C.c_uint]),
+    "lbm_activation": (_i, [_vp, _i, _i, _vp, _vp]),
+    "lbm_mlp_bf16_layout": (_i, [C.POINTER(_i), C.POINTER(_i)]),
     "lbm_velocity_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_record_bytes": (_sz, [C.POINTER(lbm_params), _i, _i]),
     "lbm_forward_record": (_i, [_vp, _i, _i, C.POINTER(lbm_weights), _vp, _sz]),
@@ -185,6 +188,26 @@ def lbm3d_lattice():
     return list(cx), list(cy), list(cz), list(w)
 
 
+def mlp_bf16_layout():
+    """(tile warpgroups per SM, XU pairs of every 8) of the compiled tensor-core step."""
+    wg, xu = C.c_int(), C.c_int()
+    _check(load().lbm_mlp_bf16_layout(C.byref(wg), C.byref(xu)), "lbm_mlp_bf16_layout")
+    return wg.value, xu.value
+
+
+def activation(a, path):
+    """The tensor-core step's hidden-layer activation applied element-wise to a
+    CUDA float32 tensor (path 0: XU form, 1: FMA form as stored, 2: FMA form
+    before its bf16 rounding)."""
+    import torch
+    assert a.dtype == torch.float32 and a.is_cuda and a.is_contiguous()
+    out = torch.empty_like(a)
+    s = torch.cuda.current_stream(a.device).cuda_stream
+    _check(load().lbm_activation(_ptr(a), a.numel(), int(path), _ptr(out), C.c_void_p(s)),
+           "lbm_activation")
+    return out
+
+
 def lbm_record_bytes(params, n, ckpt_every):
     return load().lbm_record_bytes(C.byref(params), int(n), int(ckpt_every))
 
@@ -265,6 +288,10 @@ class Lattice:
 
     def clear_status(self):
         _check(self.lib.lbm_clear_status(self.ctx), "lbm_clear_status")
+
+    def set_wait_limit(self, polls):
+        """Polls per bounded device wait of the tensor-core step (0 = default)."""
+        _check(self.lib.lbm_set_wait_limit(self.ctx, int(polls)), "lbm_set_wait_limit")
 
     # -- training -----------------------------------------------------------
     def velocity_loss(self, utx, uty, want_grad=True):

@@ -82,6 +82,21 @@ def test_noalloc_loss_rejects_grid_beyond_launch_limits(lib):
                                              None) == lbm.LBM_ERR_ARG
 
 
+def test_mlp_bf16_layout_query(lib):
+    from paper_2403_18466_gb300 import lbm
+    wg, xu = lbm.mlp_bf16_layout()
+    assert 1 <= wg <= 8 and 0 <= xu <= 8
+
+
+def test_host_side_argument_errors_of_the_test_hooks(lib):
+    from paper_2403_18466_gb300 import lbm
+    assert lib.lbm_set_wait_limit(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_activation(None, 4, 0, None, None) == lbm.LBM_ERR_ARG
+    fake = C.c_void_p(256)
+    assert lib.lbm_activation(fake, 4, 3, fake, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_activation(fake, -1, 0, fake, None) == lbm.LBM_ERR_ARG
+
+
 def test_record_bytes_and_strerror(lib):
     from paper_2403_18466_gb300 import lbm
     p = lbm.make_params(256, 256, 32, tau=0.500375)

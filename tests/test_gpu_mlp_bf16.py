@@ -1,30 +1,35 @@
-"""GPU parity of the tensor-core (tcgen05, BF16) learned collision.
+"""GPU parity of the tensor-core (tcgen05, BF16) learned collision (Eqs. S10-S12).
 
 Reference: the FP64 oracle with the SAME bf16-rounded weights, so the
-difference measures the kernel's arithmetic (bf16 activations, hardware
-tanh, FP32 accumulation), not weight quantisation; the error against the
-unrounded weights is computed too.
+difference measures the kernel's arithmetic (bf16 inputs and activations, the
+activation approximations, FP32 accumulation), not weight quantisation.  The
+error against the unrounded FP64 weights (err64) is reported for every case.
 
-Tolerance: 2e-3 relative in velocity per step.  The kernel's velocity error
-is proportional to the size of the learned correction,
-  eps_u ~ eps_bf16 * |(rho/tau) P o|_inf / |u|_inf * O(10),
-so these strongly non-linear test weights produce a correction of up to
-~1.5e-3 per population (the size of the non-equilibrium part); the plain
-Xavier weights of the 4096^2 configuration are checked as well
-(several times a typical non-equilibrium part), which stays inside 2e-3.
-Conservation is exact to FP32 rounding (the projection runs in FP32).
+Two checks per result, both able to fail for a kernel that drops the network:
+* populations, element by element: max |g - g_ref| / w_i <= ALPHA * corr, where
+  corr = max |g_ref - g_ref_BGK| / w_i is the size of the learned correction
+  (rho/tau) P o on the same scale.  ALPHA = 5e-2: every activation is rounded to
+  bf16 (relative 2^-9) and approximated (relative ~2^-8 at most), so the output
+  layer's sum of 64 such terms carries a relative error of order 1e-2 of the
+  correction; a kernel without the network has err = corr.
+* velocity per step: ||u - u_ref||_inf / ||u_ref||_inf <= TOL_U = 2e-3.
+Each test asserts that the oracle's BGK step is further than 10x the
+tolerance from the oracle's learned step (population guard, and a velocity
+guard on the first step where the lattice has more than one node per axis).
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2403_18466_gb300 import inputs
-from gpu_helpers import bf16_round, population_field, rel_vel_err, weighted_pop_err
+from gpu_helpers import (bf16_round, learned_pop_check, learned_theta, population_field,
+                         post_collision, rel_vel_err, weighted_pop_err)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 TOL_U = 2e-3
+ALPHA = 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -44,63 +49,129 @@ def _np(t):
     return t.double().cpu().numpy()
 
 
-def _theta(seed=5):
-    return inputs.xavier_mlp(seed, bias_scale=0.3, gain=3.0, out_scale=0.001)
+def _theta(seed=5, out_scale=0.0025):
+    return learned_theta(seed, out_scale=out_scale)
+
+
+def _bench_theta():
+    """The benchmark's weights (Xavier, output layer x0.3)."""
+    return inputs.xavier_mlp(3, out_scale=0.3)
 
 
 SHAPES = [(256, 64, 1), (130, 33, 2), (64, 64, 1), (37, 5, 1), (1, 1, 1), (4096, 3, 1)]
 
 
 @pytest.mark.parametrize("nx,ny,B", SHAPES)
-def test_one_step_velocity_parity(lbm, nx, ny, B):
-    tau = 0.6
+def test_one_step_population_and_velocity_parity(lbm, nx, ny, B, record_property):
+    tau, F0, m = 0.6, 1e-4, 1
     theta = _theta()
     thb = bf16_round(theta)
     f = population_field(B, ny, nx, seed=nx + 3 * ny)
-    lat = lbm.Lattice(nx, ny, B, tau=tau, force_amp=1e-4, force_mode=1, device=DEV)
+    lat = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
     w = lbm.weights_struct(_dev(theta))
     lat.set_state(_dev(f))
     g = oracle.stream_push(f.astype(np.float64))
-    prm = oracle.params(tau, force_amp=1e-4, force_mode=1)
+    prm = oracle.params(tau, force_amp=F0, force_mode=m)
     for step in range(2):
-        g_in = g
         lat.step(1, "mlp_bf16", w)
-        g = oracle.step(oracle.MLP, g_in, prm, thb)
+        ref = oracle.step(oracle.MLP, g, prm, thb)
+        ref_bgk = oracle.step(oracle.BGK, g, prm)
+        ref64 = oracle.step(oracle.MLP, g, prm, theta)
+        got = post_collision(lat)
+        ok, err, corr, tol = learned_pop_check(got, ref, ref_bgk, ALPHA)
+        err64 = weighted_pop_err(got, ref64)
         _, gx, gy = (_np(t) for t in lat.moments())
-        _, rx, ry = oracle.moments(oracle.stream_pull(g))
-        err = rel_vel_err(gx, gy, rx, ry)
-        assert err <= TOL_U, err
-        # FP64 error against the unrounded weights, reported through the assert message
-        g64 = oracle.step(oracle.MLP, g_in, prm, theta)
-        _, sx, sy = oracle.moments(oracle.stream_pull(g64))
-        err64 = rel_vel_err(gx, gy, sx, sy)
-        assert np.isfinite(err64), err64
+        _, rx, ry = oracle.moments(oracle.stream_pull(ref))
+        _, bx, by = oracle.moments(oracle.stream_pull(ref_bgk))
+        _, sx, sy = oracle.moments(oracle.stream_pull(ref64))
+        eu, eu64, du = rel_vel_err(gx, gy, rx, ry), rel_vel_err(gx, gy, sx, sy), \
+            rel_vel_err(bx, by, rx, ry)
+        msg = (f"{nx}x{ny}x{B} step {step}: pop err {err:.3e} (tol {tol:.3e}, correction "
+               f"{corr:.3e}, err/corr {err / corr:.3e}), err64 {err64:.3e}; velocity err "
+               f"{eu:.3e}, err64 {eu64:.3e}, BGK-vs-learned {du:.3e}")
+        print(msg)
+        record_property(f"step{step}", msg)
+        assert corr > 10 * tol and corr > 1e-2, msg  # the guard: BGK is far outside
+        assert ok, msg
+        # velocity: a well-conditioned probe of the kernel where the learned part
+        # moves the velocity by a few per cent (the kernel's velocity error is
+        # ~2 % of that move); on the thin lattices the second step moves it by
+        # 30-60 % of a tiny |u|, and only the population check applies there
+        if du <= 0.08:
+            assert eu <= TOL_U, msg
+        if step == 0 and nx > 1 and ny > 1:
+            assert du > 10 * TOL_U, msg
         # continue both from the GPU state so the check stays per step
-        g = oracle.stream_push(_np(lat.get_state()))
+        g = got  # post-collision populations, float64
     assert lat.status() == lbm.LBM_OK
 
 
 def test_config_xavier_weights_4096_wide(lbm):
-    """Plain seeded Xavier weights (zero biases), as in the 4096^2 configuration."""
-    nx, ny, tau = 4096, 8, 0.6
+    """Plain seeded Xavier weights (zero biases) of the 4096^2 configuration."""
+    nx, ny, tau, F0, m = 4096, 8, 0.6, 1e-5, 4
     theta = inputs.xavier_mlp(3)
     thb = bf16_round(theta)
     f = population_field(1, ny, nx, seed=17)
-    lat = lbm.Lattice(nx, ny, 1, tau=tau, force_amp=1e-5, force_mode=4, device=DEV)
+    lat = lbm.Lattice(nx, ny, 1, tau=tau, force_amp=F0, force_mode=m, device=DEV)
     lat.set_state(_dev(f))
     lat.step(1, "mlp_bf16", lbm.weights_struct(_dev(theta)))
-    g = oracle.step(oracle.MLP, oracle.stream_push(f.astype(np.float64)),
-                    oracle.params(tau, force_amp=1e-5, force_mode=4), thb)
+    g0 = oracle.stream_push(f.astype(np.float64))
+    prm = oracle.params(tau, force_amp=F0, force_mode=m)
+    ref = oracle.step(oracle.MLP, g0, prm, thb)
+    ref_bgk = oracle.step(oracle.BGK, g0, prm)
+    ok, err, corr, tol = learned_pop_check(post_collision(lat), ref, ref_bgk, ALPHA)
+    err64 = weighted_pop_err(post_collision(lat), oracle.step(oracle.MLP, g0, prm, theta))
     _, gx, gy = (_np(t) for t in lat.moments())
-    _, rx, ry = oracle.moments(oracle.stream_pull(g))
-    assert rel_vel_err(gx, gy, rx, ry) <= TOL_U
+    _, rx, ry = oracle.moments(oracle.stream_pull(ref))
+    _, bx, by = oracle.moments(oracle.stream_pull(ref_bgk))
+    msg = (f"pop err {err:.3e} (correction {corr:.3e}, err/corr {err / corr:.3e}), "
+           f"err64 {err64:.3e}; velocity err {rel_vel_err(gx, gy, rx, ry):.3e}")
+    print(msg)
+    assert corr > 10 * tol and ok, msg
+    assert rel_vel_err(gx, gy, rx, ry) <= TOL_U, msg
+    assert rel_vel_err(bx, by, rx, ry) > 10 * TOL_U, msg
+
+
+@pytest.mark.parametrize("kind", ["mlp_bf16", "mlp_f32"])
+def test_conservation_per_node(lbm, kind):
+    """Eqs. S11-S12: at every node the collision keeps the mass and changes the
+    momentum by exactly the force: |sum g - sum f| <= 1e-6 rho and
+    |sum g c - sum f c - F| <= 1e-6 (pre-collision f gathered just before the
+    step, post-collision g read from the state buffer after it)."""
+    nx, ny, B, tau, F0, m = 256, 64, 2, 0.6, 1e-4, 1
+    theta = _theta(11)
+    lat = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
+    lat.set_state(_dev(population_field(B, ny, nx, seed=21)))
+    w = lbm.weights_struct(_dev(theta))
+    lat.step(2, kind, w)  # a developed state
+    cx, cy, _ = oracle.lattice()
+    pre = _np(lat.get_state())
+    lat.step(1, kind, w)
+    post = post_collision(lat)
+    assert lat.status() == lbm.LBM_OK
+    rho = pre.sum(1)
+    dm = np.abs(post.sum(1) - rho)
+    Fx = F0 * np.sin(2 * np.pi * m * np.arange(ny) / ny)[None, :, None]
+    djx = np.abs(np.einsum("biyx,i->byx", post - pre, cx) - Fx)
+    djy = np.abs(np.einsum("biyx,i->byx", post - pre, cy))
+    # the correction is far from conserving by accident: it moves populations
+    # by more than the tolerances below
+    bgk = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
+    bgk.set_state(_dev(pre))
+    bgk.step(1, "bgk")
+    moved = np.abs(post_collision(bgk) - post).max()
+    print(f"{kind}: max mass defect / rho {(dm / rho).max():.3e}, momentum defect "
+          f"{max(djx.max(), djy.max()):.3e}, correction {moved:.3e}")
+    assert moved > 1e-3
+    assert (dm <= 1e-6 * rho).all(), (dm / rho).max()
+    assert (djx <= 1e-6).all() and (djy <= 1e-6).all(), (djx.max(), djy.max())
 
 
 def test_conservation_and_mass_drift(lbm):
     n = 256
     f = population_field(1, n, n, seed=7)
     lat = lbm.Lattice(n, n, 1, tau=0.55, device=DEV)
-    w = lbm.weights_struct(_dev(_theta(9)))
+    w = lbm.weights_struct(_dev(_theta(9, out_scale=0.002)))
     lat.set_state(_dev(f))
     m0 = float(_np(lat.get_state()).sum())
     cx, cy, _ = oracle.lattice()
@@ -141,57 +212,101 @@ def test_bf16_weight_input_matches_f32_input(lbm):
 
 
 def test_bf16_close_to_f32_kernel(lbm):
-    """The two learned-collision kernels agree to the bf16 error level."""
+    """The two learned-collision kernels agree to the bf16 error level, on the
+    population scale of the learned correction (the FP32 kernel is the
+    reference here, BGK the guard)."""
     theta = _theta(8)
     f = population_field(1, 64, 512, seed=8)
     res = {}
-    for kind in ("mlp_bf16", "mlp_f32"):
+    for kind in ("mlp_bf16", "mlp_f32", "bgk"):
         lat = lbm.Lattice(512, 64, 1, tau=0.6, device=DEV)
         lat.set_state(_dev(f))
         lat.step(1, kind, lbm.weights_struct(_dev(theta)))
-        res[kind] = [_np(t) for t in lat.moments()]
-    assert rel_vel_err(res["mlp_bf16"][1], res["mlp_bf16"][2], res["mlp_f32"][1],
-                       res["mlp_f32"][2]) <= TOL_U
+        res[kind] = post_collision(lat)
+    ok, err, corr, tol = learned_pop_check(res["mlp_bf16"], res["mlp_f32"], res["bgk"], ALPHA)
+    print(f"bf16 vs f32 kernel: pop err {err:.3e}, correction {corr:.3e}")
+    assert corr > 10 * tol and ok, (err, corr)
 
 
-@pytest.mark.parametrize("kind", ["mlp_bf16", "bgk"])
-def test_full_size_4096_sampled_nodes(lbm, kind):
+@pytest.mark.parametrize("kind,weights", [("mlp_bf16", "bench"), ("mlp_bf16", "nonlinear"),
+                                          ("bgk", None)])
+def test_full_size_4096_sampled_nodes(lbm, kind, weights):
     """The benchmark's 4096^2 configuration, one step in the benchmark's launch
-    configuration; sampled nodes checked one by one against the oracle: the
-    velocity at t+1 of a node needs the oracle's collision at its 9 upstream
-    neighbours."""
-    n, tau = 4096, 0.6
+    configuration; 300 sampled nodes checked one by one against the oracle.
+    The stored pre-collision population i of node x at t+1 is the oracle's
+    post-collision population i of the upstream node x - c_i at t, so each
+    sample needs the oracle's collision at its 9 upstream neighbours."""
+    n, tau, F0, m = 4096, 0.6, 1e-5, 4
     rho, ux, uy = inputs.random_velocity_field(n, n, seed=2, k0=8.0, urms=0.02)
-    lat = lbm.Lattice(n, n, 1, tau=tau, force_amp=1e-5, force_mode=4, device=DEV)
+    lat = lbm.Lattice(n, n, 1, tau=tau, force_amp=F0, force_mode=m, device=DEV)
     lat.init_equilibrium(_dev(rho[None]), _dev(ux[None]), _dev(uy[None]))
-    theta = _theta(3)
+    theta = _bench_theta() if weights == "bench" else _theta(3)
     w = lbm.weights_struct(_dev(theta))
     lat.step(2, kind, w)  # develop a non-equilibrium part
     f0 = lat.get_state()[0]
     lat.step(1, kind, w)
     f1 = lat.get_state()[0]
     assert lat.status() == lbm.LBM_OK
-    cx, cy, _ = oracle.lattice()
+    cx, cy, wts = oracle.lattice()
     rng = np.random.default_rng(0)
     ys, xs = rng.integers(0, n, 300), rng.integers(0, n, 300)
     ys[:4], xs[:4] = [0, 0, n - 1, n - 1], [0, n - 1, 0, n - 1]  # periodic corners
     thb = bf16_round(theta)
     prm = oracle.params(tau)
     okind = oracle.MLP if kind == "mlp_bf16" else oracle.BGK
-    Fy = 1e-5 * np.sin(2 * np.pi * 4 * np.arange(n) / n)
-    errs = []
-    for y, x in zip(ys, xs):
-        post = np.empty(9)
+    Fx = F0 * np.sin(2 * np.pi * m * np.arange(n) / n)
+    got, ref, ref_bgk, ref64 = (np.empty((len(ys), 9)) for _ in range(4))
+    for s, (y, x) in enumerate(zip(ys, xs)):
         for i in range(9):
             yu, xu = (y - cy[i]) % n, (x - cx[i]) % n  # upstream node of population i
             fu = f0[:, yu, xu].double().cpu().numpy()
-            post[i] = oracle.collide_node(okind, fu, prm, thb, Fy[yu], 0.0)[i]
-        ref_u = np.array([post @ cx, post @ cy]) / post.sum()
-        g = f1[:, y, x].double().cpu().numpy()
-        gu = np.array([g @ cx, g @ cy]) / g.sum()
-        errs.append(np.abs(gu - ref_u).max())
-        if kind == "bgk":
-            assert weighted_pop_err(g[None, :, None, None], post[None, :, None, None]) <= 1e-5
+            ref[s, i] = oracle.collide_node(okind, fu, prm, thb, Fx[yu], 0.0)[i]
+            ref_bgk[s, i] = oracle.collide_node(oracle.BGK, fu, prm, None, Fx[yu], 0.0)[i]
+            ref64[s, i] = oracle.collide_node(okind, fu, prm, theta, Fx[yu], 0.0)[i]
+        got[s] = f1[:, y, x].double().cpu().numpy()
+    err_u = []
+    for s in range(len(ys)):
+        ru = np.array([ref[s] @ cx, ref[s] @ cy]) / ref[s].sum()
+        gu = np.array([got[s] @ cx, got[s] @ cy]) / got[s].sum()
+        err_u.append(np.abs(gu - ru).max())
     _, vx, vy = lat.moments()
     umax = max(vx.abs().max().item(), vy.abs().max().item())
-    assert max(errs) / umax <= (TOL_U if kind == "mlp_bf16" else 1e-5)
+    eu = max(err_u) / umax
+    err64 = float(np.max(np.abs(got - ref64) / wts[None, :]))
+    if kind == "bgk":
+        assert float(np.max(np.abs(got - ref) / wts[None, :])) <= 1e-5
+        assert eu <= 1e-5
+        return
+    ok, err, corr, tol = learned_pop_check(got, ref, ref_bgk, ALPHA)
+    msg = (f"4096^2 {weights}: pop err {err:.3e} (correction {corr:.3e}, err/corr "
+           f"{err / corr:.3e}), err64 {err64:.3e}; velocity err {eu:.3e}")
+    print(msg)
+    assert corr > 10 * tol and ok, msg
+    assert eu <= TOL_U, msg
+
+
+def test_bounded_wait_timeout_and_recovery(lbm):
+    """Failure detection without a fault: a wait limit of one non-blocking poll
+    makes every warpgroup's first GEMM wait give up; the step stops, frees its
+    tensor memory and lbm_status reports LBM_ERR_TIMEOUT.  After clearing the
+    status and restoring the default limit the next step is bitwise the same
+    as on a lattice that never timed out."""
+    nx, ny = 1024, 64
+    theta = _theta(12)
+    w = lbm.weights_struct(_dev(theta))
+    f = _dev(population_field(1, ny, nx, seed=31))
+    a = lbm.Lattice(nx, ny, 1, tau=0.6, force_amp=1e-5, force_mode=1, device=DEV)
+    b = lbm.Lattice(nx, ny, 1, tau=0.6, force_amp=1e-5, force_mode=1, device=DEV)
+    a.set_wait_limit(1)
+    a.set_state(f)
+    a.step(1, "mlp_bf16", w)
+    assert a.status() == lbm.LBM_ERR_TIMEOUT
+    a.clear_status()
+    a.set_wait_limit(0)
+    assert a.status() == lbm.LBM_OK
+    a.set_state(f)
+    b.set_state(f)
+    a.step(2, "mlp_bf16", w)
+    b.step(2, "mlp_bf16", w)
+    assert a.status() == lbm.LBM_OK and b.status() == lbm.LBM_OK
+    assert torch.equal(a.get_state(), b.get_state())
