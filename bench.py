@@ -38,6 +38,9 @@ MLP_FLOP_PER_NODE = 2 * (9 * 64 + 64 * 64 + 64 * 9)  # 10,496 algorithmic flops 
 # the learned collision blow up within ~100 steps; 0.3 stays stable for >1500.
 OUT_SCALE = 0.3
 MLP_BF16_SOURCES = ("mlp_bf16.cu", "lattice.cuh", "umma.cuh", "kernels.h")
+# Sub-partition cycles one warp-wide cvt.rn.bf16x2.f32 + tanh.approx.bf16x2 pair
+# holds the XU (measured, profiles/activation_units_microbenchmark.md).
+XU_PAIR_CYCLES = 16.42
 WORKLOAD = ("D2Q9 learned-collision LBM step (MLP 9-64-64-9 tanh on tcgen05 BF16, FP32 "
             "populations), periodic 4096x4096, Kolmogorov forcing F0=1e-5 m=4, tau=0.6, "
             "random-phase initial field (rms 0.02, seed 2), Xavier weights (seed 3, output "
@@ -214,23 +217,29 @@ def run_gpu(args):
 
     # ---- roofline of the dominant kernel (the step kernel itself) ---------
     achieved_gbs = BYTES_PER_NODE * nodes / (ms / args.steps * 1e-3) / 1e9
-    # binding unit of the learned step: the XU (special-function) pipe.  Each
-    # node needs 64 tanh.approx.bf16x2 and 64 cvt.rn.bf16x2.f32 (the 128
-    # activations of the two hidden layers).  Measured on this GPU with that
-    # instruction mix (cvt + tanh per pair, packed stores, 16 warps per SM):
-    # 0.239 tanh.bf16x2 warp instructions per cycle per SM, i.e. one node per
-    # 64 / 32 / 0.239 = 8.37 cycles per SM (1 warp per sub-partition reaches
-    # only half of that).
-    xu_cycles_per_node_per_sm = 64 / 32 / 0.239
+    # binding unit of the learned step: the XU (special-function) pipe.  Of
+    # every 8 pairs of hidden units the compiled kernel sends `xu8` to the XU
+    # (cvt.rn.bf16x2.f32 + tanh.approx.bf16x2) and the rest to the FMA pipe.
+    # Measured on this GPU (profiles/activation_units_microbenchmark.md): one
+    # warp-wide XU pair holds an SM sub-partition's XU for 16.42 cycles.  A node
+    # has 64 pairs, so the XU needs 64 * xu8/8 * 16.42 / 32 sub-partition cycles
+    # per node, a quarter of that in SM cycles.
+    wg_per_sm, xu8 = lbm.mlp_bf16_layout()
+    xu_sm_cycles_per_node = 64 * (xu8 / 8.0) * XU_PAIR_CYCLES / 32 / 4
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    xu_bound = sms * sm_mhz * 1e6 / xu_cycles_per_node_per_sm / 1e6  # MLUPS per GPU
-    binding = {"unit": "xu (tanh + bf16x2 conversion)", "achieved": round(nodes / (ms / args.steps * 1e-3) / 1e6, 1),
-               "peak": round(xu_bound, 1), "peak_unit": "MLUPS",
-               "frac": round(nodes / (ms / args.steps * 1e-3) / 1e6 / xu_bound, 4),
-               "derivation": "64 tanh.approx.bf16x2 + 64 cvt.rn.bf16x2.f32 per node; measured "
-                             "XU throughput with that mix 0.239 tanh warp-instr/cycle/SM "
-                             "(16 warps/SM); measured SM clock"}
+    node_rate = nodes / (ms / args.steps * 1e-3) / 1e6  # MLUPS per GPU
+    xu_bound = sms * sm_mhz * 1e6 / xu_sm_cycles_per_node / 1e6 if xu8 else float("inf")
+    binding = {"unit": "xu (tanh.approx.bf16x2 + cvt.rn.bf16x2.f32 of the XU pairs)",
+               "achieved": round(node_rate, 1), "peak": round(xu_bound, 1), "peak_unit": "MLUPS",
+               "frac": round(node_rate / xu_bound, 4),
+               "sm_cycles_per_node": round(sms * sm_mhz * 1e6 / (node_rate * 1e6), 3),
+               "xu_sm_cycles_per_node": round(xu_sm_cycles_per_node, 3),
+               "time_x_sm_mhz": round(ms / args.steps * sm_mhz, 2),
+               "kernel_layout": {"warpgroups_per_sm": wg_per_sm, "xu_pairs_of_8": xu8},
+               "derivation": f"64 hidden-unit pairs per node, {xu8} of 8 on the XU at "
+                             f"{XU_PAIR_CYCLES} sub-partition cycles per warp-wide pair "
+                             "(measured), 4 sub-partitions per SM, measured SM clock"}
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
                 "traffic": _traffic_from_profile(MLP_BF16_SOURCES, "k_step_mlp_bf16_2048.md", nodes),

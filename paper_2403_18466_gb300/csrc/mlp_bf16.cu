@@ -10,40 +10,46 @@
 // Work decomposition.  A tile is 128 consecutive nodes of one row; a
 // warpgroup (128 threads, thread r = node r = tensor-memory lane r) owns one
 // tile at a time and walks its own contiguous range of tiles; one persistent
-// CTA per SM holds WGS warpgroups.  Each layer is one GEMM with M = 128 nodes
-// and BOTH activation operands in tensor memory (tcgen05.mma with A in TMEM):
+// CTA per SM holds WGS = 8 warpgroups (1024 threads, 64 registers each, all
+// 512 tensor-memory columns), so that many warps are in their activation
+// epilogues at once.  Each layer is one GEMM with M = 128 nodes, BF16
+// operands in shared memory (canonical K-major, no swizzle), FP32
+// accumulators in the warpgroup's 64 tensor-memory columns:
 //   layer 1: [128 x 16] x [16 x 64]   K = 9 inputs + a constant-1 column (b1) + 6 zeros
-//   layer 2: [128 x 64] x [64 x 64]   + [128 x 16 ones-column] x [16 x 64 (b2 | 0)]
-//   layer 3: [128 x 64] x [64 x 16]   + the same ones-column x [16 x 16 (b3 | 0)]
-// The per-tile tensor memory is the accumulator (64 columns) and the bf16 A
-// operand (64 values = 32 columns): 96 columns, 5 tiles per SM plus one shared
-// 8-column block whose first K element is 1 in every lane (the A operand of
-// the bias MMAs).  Only the weights (14.5 KB per tile) are read from shared
-// memory by the tensor core, so the GEMMs do not compete with anything else
-// for the SM's shared-memory bandwidth.
+//   layer 2: [128 x 80] x [80 x 64]   K = 64 hidden + constant-1 column (b2) + 15 zeros
+//   layer 3: [128 x 80] x [80 x 16]   N = 9 outputs + 7 zero columns, b3 via the 1-column
+// so the biases ride on the MMA.  (Keeping the activations in tensor memory
+// as the A operand instead needs 96 columns per tile, i.e. 5 tiles per SM; at
+// that depth the GEMM round trips were no longer hidden: 21 G against 25 G
+// nodes/s.)
 //
 // Between layers each thread reads its accumulator row with tcgen05.ld,
-// applies tanh and writes the bf16 row back as the next A operand with
-// tcgen05.st.  The activations are split between two units (TANH_XU_PAIRS of
-// every 8 pairs on the XU, the rest on the FMA pipe), because the XU alone
-// caps the step near 40 G nodes/s:
-//   XU pairs:  cvt.rn.bf16x2.f32, then tanh.approx.bf16x2;
+// applies tanh and writes the bf16 row of the next A operand to shared
+// memory with 128-bit stores.  The activations are split between two units
+// (TANH_XU_PAIRS of every 8 pairs of hidden units on the XU, the rest on the
+// FMA pipe):
+//   XU pairs:  cvt.rn.bf16x2.f32, then tanh.approx.bf16x2 (16.4 cycles of an
+//     SM sub-partition per warp-wide pair, measured);
 //   FMA pairs: the hidden units' weight rows and biases are pre-scaled by 1/4
 //     (exact in bf16), so the accumulator holds y = a/4;  u = min(y^2, 1)
 //     (fma.sat), tanh(a) ~ y P(u) with the degree-8 relative minimax
 //     polynomial P of tanh(4 sqrt(u))/sqrt(u) on [0, 1] (odd in y, so small
 //     activations keep their relative accuracy) in packed fma.rn.f32x2,
 //     rounded to bf16 (cvt.rn) and clamped to [-1, 1] (min.xorsign.abs).
-//     Maximum error before the rounding: 0.36 bf16 ulp of tanh (half-ulp bar
-//     checked in float32 and on the GPU against tanhf); |a| >= 4 gives +-1,
+//     Maximum error before the rounding: 0.36 bf16 ulp of tanh (0.71 of the
+//     half-ulp bar, checked on the GPU against tanhf); |a| >= 4 gives +-1,
 //     which is the bf16 rounding of tanh(a) there.
+// The FMA form takes ~26 cycles per warp-wide pair in isolation against 16.4
+// for the XU form, and 13 issue slots against 2, so it pays only as a small
+// share next to the kernel's other work (measured at 4096^2: 8 of 8 pairs on
+// the XU 25.2 G nodes/s, 7 of 8: 25.3 G, 6: 25.1 G, 4: 20.3 G).
 //
 // Per node the moments, equilibrium, x and the BGK + force update are
 // computed once, while the previous tile's last GEMM runs; the epilogue of
 // layer 3 only projects o and adds (rho/tau) P o to the stored update.
 //
-// Synchronisation per warpgroup: tensor-memory stores of all 128 threads ->
-// tcgen05.wait::st + fence::before_thread_sync + named barrier -> one thread
+// Synchronisation per warpgroup: operand rows written by all 128 threads ->
+// fence.proxy.async + fence::before_thread_sync + named barrier -> one thread
 // issues the MMAs and commits them to the warpgroup's mbarrier -> that thread
 // alone polls the mbarrier (bounded) while the others sleep in a named
 // barrier that also carries its verdict (bar.red.or), so a time-out is seen by
@@ -63,10 +69,10 @@ using namespace umma;
 
 constexpr int WG_THREADS = 128;
 #ifndef LBM_BF16_WGS
-#define LBM_BF16_WGS 5
+#define LBM_BF16_WGS 8
 #endif
 #ifndef LBM_TANH_XU_PAIRS
-#define LBM_TANH_XU_PAIRS 5
+#define LBM_TANH_XU_PAIRS 7
 #endif
 #ifndef LBM_TANH_XU_FORM
 #define LBM_TANH_XU_FORM 0
@@ -82,15 +88,17 @@ constexpr int XU_FORM = LBM_TANH_XU_FORM;
 // bf16 packing of the FMA form: 0 = cvt.rn.bf16x2.f32 (XU), 1 = integer
 // rounding on the ALU (ties away from zero)
 constexpr int FMA_PACK = LBM_TANH_FMA_PACK;
+#ifndef LBM_LEADER_SPREAD
+#define LBM_LEADER_SPREAD 1
+#endif
+constexpr bool LEADER_SPREAD = LBM_LEADER_SPREAD != 0;
 constexpr int THREADS = WGS * WG_THREADS;
 constexpr int XU_PAIRS = LBM_TANH_XU_PAIRS;  // of every 8 activation pairs, on the XU
 static_assert(XU_PAIRS >= 0 && XU_PAIRS <= 8, "split of 8 pairs");
-constexpr int K1 = 16, KH = 64, KB = 16;  // K of layer 1, of the hidden GEMMs, of the bias MMAs
-// tensor memory: per warpgroup the accumulator [0, 64) and the A operand
-// [64, 96); the shared ones-column block after the last warpgroup
-constexpr uint32_t WG_COLS = 96, C_ACC = 0, C_A = 64, C_ONE = WGS * WG_COLS;
+constexpr int K1 = 16, K2 = 80;  // padded K of layer 1 and of layers 2/3
+// tensor memory: 64 accumulator columns per warpgroup
 constexpr uint32_t TMEM_COLS = 512;
-static_assert(C_ONE + 8 <= TMEM_COLS, "tensor memory layout");
+static_assert(WGS * 64 <= (int)TMEM_COLS, "tensor memory layout");
 constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 20;  // polls; far above any real MMA latency
 
 // Bounded wait for a GEMM's commit.  A limit of 1024 polls or more uses
@@ -117,11 +125,11 @@ constexpr float TP0 = 3.9946699142456055f, TP1 = -20.35879898071289f, TP2 = 103.
 __host__ __device__ constexpr bool fma_unit(int n) { return (n % 16) >= 2 * XU_PAIRS; }
 
 struct __align__(1024) Smem {
-  unsigned char w1[HIDDEN * K1 * 2];  // B of layer 1: [64 x 16] = W1 | b1 | 0
-  unsigned char w2[HIDDEN * KH * 2];  // B of layer 2: [64 x 64] = W2
-  unsigned char w3[16 * KH * 2];      // B of layer 3: [16 x 64] = W3 | 0 rows
-  unsigned char bb2[HIDDEN * KB * 2]; // [64 x 16]: column 0 = b2
-  unsigned char bb3[16 * KB * 2];     // [16 x 16]: column 0 = b3
+  unsigned char w1[HIDDEN * K1 * 2];     // B of layer 1: [64 x 16] = W1 | b1 | 0
+  unsigned char w2[HIDDEN * K2 * 2];     // B of layer 2: [64 x 80] = W2 | b2 | 0
+  unsigned char w3[16 * K2 * 2];         // B of layer 3: [16 x 80] = W3 | b3 | 0, rows 9..15 zero
+  unsigned char a1[WGS][128 * K1 * 2];   // A of layer 1, per warpgroup
+  unsigned char a23[WGS][128 * K2 * 2];  // A of layers 2 and 3, per warpgroup
   unsigned long long bar[WGS];
   uint32_t taddr;
 };
@@ -192,21 +200,25 @@ __device__ __forceinline__ uint32_t act_fma(float y0, float y1) {
   return clamp_unit_bf16x2(FMA_PACK == 1 ? pack_bf16x2_alu(h0, h1) : pack_bf16x2(h0, h1));
 }
 
-// Accumulator columns [0, 64) of this thread's row -> tanh -> bf16 pairs in
-// A-operand columns [C_A, C_A + 32) of the same row.
-__device__ __forceinline__ void hidden_epilogue(uint32_t tm_row) {
+// Accumulator columns [0, 64) of this thread's row -> tanh -> bf16 pairs as
+// K columns 0..63 of row r of the layer-2/3 operand (16 columns at a time,
+// within the 64-register budget).
+__device__ __forceinline__ void hidden_epilogue(uint32_t tm_row, unsigned char *a23, int r) {
 #pragma unroll
-  for (int c = 0; c < HIDDEN; c += 32) {
-    uint32_t v[32];
-    tmem_ld32(tm_row + C_ACC + c, v);
+  for (int c = 0; c < HIDDEN; c += 16) {
+    uint32_t v[16];
+    tmem_ld16(tm_row + c, v);
     tmem_wait_ld();
-    uint32_t p[16];
+    uint32_t p[8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const float a0 = __uint_as_float(v[2 * q]), a1 = __uint_as_float(v[2 * q + 1]);
       p[q] = fma_unit(c + 2 * q) ? act_fma(a0, a1) : act_xu(a0, a1);
     }
-    tmem_st16(tm_row + C_A + c / 2, p);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8 * q, K2)) =
+          make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
 }
 
@@ -242,35 +254,33 @@ __device__ __forceinline__ void pull_node(const float *__restrict__ in, size_t p
 }
 
 // Everything of a node's update that does not need the network: moments,
-// x = (f - feq)/rho as the layer-1 operand row (9 inputs, the constant-1 bias
-// column, zeros; bf16 with integer rounding on the ALU), the BGK + force
-// update (the same helpers as the BGK kernel, so a zero output layer
-// reproduces BGK bit for bit) and rho/tau.
+// x = (f - feq)/rho written as row r of the layer-1 operand (9 inputs, the
+// constant-1 bias column, zeros; bf16 with integer rounding on the ALU), the
+// BGK + force update (the same helpers as the BGK kernel, so a zero output
+// layer reproduces BGK bit for bit) and rho/tau.  Returns true for an
+// unstable node.
 struct NodePrep {
-  uint32_t xp[8];
   float base[Q];
   float rw;
-  bool bad;
 };
-__device__ __forceinline__ void prep_node(const float d[Q], float omega, const float *force,
-                                          float fx, NodePrep &P) {
+__device__ __forceinline__ bool prep_node(const float d[Q], float omega, const float *force,
+                                          float fx, unsigned char *a1, int r, NodePrep &P) {
   const Moments m = node_moments(d);
-  P.bad = is_unstable(m);
   float deq[Q];
   shifted_feq(m, deq);
   float xin[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * m.inv_rho;
-  P.xp[0] = pack_bf16x2_alu(xin[0], xin[1]);
-  P.xp[1] = pack_bf16x2_alu(xin[2], xin[3]);
-  P.xp[2] = pack_bf16x2_alu(xin[4], xin[5]);
-  P.xp[3] = pack_bf16x2_alu(xin[6], xin[7]);
-  P.xp[4] = pack_bf16x2_alu(xin[8], 1.0f);
-  P.xp[5] = P.xp[6] = P.xp[7] = 0u;
+  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
+      make_uint4(pack_bf16x2_alu(xin[0], xin[1]), pack_bf16x2_alu(xin[2], xin[3]),
+                 pack_bf16x2_alu(xin[4], xin[5]), pack_bf16x2_alu(xin[6], xin[7]));
+  *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
+      make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) P.base[i] = fmaf(omega, deq[i] - d[i], d[i]);
   if (force) add_edm_force_x(m, fx, P.base);
   P.rw = m.rho * omega;
+  return is_unstable(m);
 }
 
 // f' = base + (rho/tau) P o, with P the projection removing span{1, c_x, c_y}
@@ -305,34 +315,32 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int r = tid % WG_THREADS;   // row = node within the tile = TMEM lane
   const int warp_in_wg = r / 32;
 
-  // ---- prologue: weights -> bf16 operand tiles (FMA-path units pre-scaled
-  // by 1/4, exact in bf16), barriers, tensor memory, the ones-column block
+  // ---- prologue: weights -> bf16 operand tiles (FMA-form units pre-scaled
+  // by 1/4, exact in bf16), constant columns, barriers, tensor memory
   for (int e = tid; e < HIDDEN * K1; e += THREADS) {
     const int n = e / K1, k = e % K1;
     float v = k < 9 ? wload<DTYPE>(w1, n * 9 + k) : (k == 9 ? wload<DTYPE>(b1, n) : 0.f);
     if (fma_unit(n)) v *= 0.25f;
     store_bf16(S.w1, n, k, K1, v);
   }
-  for (int e = tid; e < HIDDEN * KH; e += THREADS) {
-    const int n = e / KH, k = e % KH;
-    float v = wload<DTYPE>(w2, n * HIDDEN + k);
+  for (int e = tid; e < HIDDEN * K2; e += THREADS) {
+    const int n = e / K2, k = e % K2;
+    float v = k < HIDDEN ? wload<DTYPE>(w2, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b2, n) : 0.f);
     if (fma_unit(n)) v *= 0.25f;
-    store_bf16(S.w2, n, k, KH, v);
+    store_bf16(S.w2, n, k, K2, v);
   }
-  for (int e = tid; e < 16 * KH; e += THREADS) {
-    const int n = e / KH, k = e % KH;
-    store_bf16(S.w3, n, k, KH, n < 9 ? wload<DTYPE>(w3, n * HIDDEN + k) : 0.f);
+  for (int e = tid; e < 16 * K2; e += THREADS) {
+    const int n = e / K2, k = e % K2;
+    float v = 0.f;
+    if (n < 9)
+      v = k < HIDDEN ? wload<DTYPE>(w3, n * HIDDEN + k) : (k == HIDDEN ? wload<DTYPE>(b3, n) : 0.f);
+    store_bf16(S.w3, n, k, K2, v);
   }
-  for (int e = tid; e < HIDDEN * KB; e += THREADS) {
-    const int n = e / KB, k = e % KB;
-    float v = k == 0 ? wload<DTYPE>(b2, n) : 0.f;
-    if (fma_unit(n)) v *= 0.25f;
-    store_bf16(S.bb2, n, k, KB, v);
-  }
-  for (int e = tid; e < 16 * KB; e += THREADS) {
-    const int n = e / KB, k = e % KB;
-    store_bf16(S.bb3, n, k, KB, (k == 0 && n < 9) ? wload<DTYPE>(b3, n) : 0.f);
-  }
+  unsigned char *a1 = S.a1[wg];
+  unsigned char *a23 = S.a23[wg];
+  // constant K columns 64..79 of this thread's layer-2/3 operand row: 1, 0, ..., 0
+  *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4 *>(a23 + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int k = 0; k < WGS; ++k) mbar_init(smem_u32(&S.bar[k]), 1);
     fence_mbarrier_init();
@@ -346,25 +354,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after_sync();
 
-  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * WG_COLS);               // this WG's columns
-  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);      // + lane base
-  if (wg == 0) {  // the ones-column block: K element 0 = 1 in every lane
-    const uint32_t one[8] = {0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    tmem_st8(S.taddr + C_ONE + ((uint32_t)(32 * warp_in_wg) << 16), one);
-    tmem_wait_st();
-  }
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-
+  const uint32_t tm_wg = S.taddr + (uint32_t)(wg * 64);                // this WG's columns
+  const uint32_t tm_row = tm_wg + ((uint32_t)(32 * warp_in_wg) << 16);  // + lane base
   const uint32_t bar = smem_u32(&S.bar[wg]);
   const uint32_t bar_id = 1 + wg;
-  const bool leader = r == 0;
-  const uint32_t a_op = tm_wg + C_A, acc = tm_wg + C_ACC, ones = S.taddr + C_ONE;
-  const uint64_t dw1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
-  const uint64_t dbb2 = smem_desc(smem_u32(S.bb2), 128, 16 * KB);
-  const uint64_t dbb3 = smem_desc(smem_u32(S.bb3), 128, 16 * KB);
-  const uint32_t sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
+  // the thread that issues and waits for the warpgroup's GEMMs: lane 0 of
+  // warp (wg mod 4) of the warpgroup, so that the eight leaders sit on all
+  // four SM sub-partitions (CTA warp w runs on sub-partition w mod 4)
+  const bool leader = LEADER_SPREAD ? r == 32 * (wg & 3) : r == 0;
+  const uint64_t da1 = smem_desc(smem_u32(a1), 128, 16 * K1);
+  const uint64_t db1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
+  const uint32_t sa23 = smem_u32(a23), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
   constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
 
   // ---- this warpgroup's contiguous range of tiles
@@ -393,23 +393,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int i = 0; i < Q; ++i) d[i] = 0.f;
     const bool act = count > 0 && T.x0 + r < nx;
     if (act) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
-    prep_node(d, omega, p.force, (count > 0 && p.force) ? __ldg(p.force + T.y) : 0.f, P);
-    bad = act && P.bad;
-    tmem_st8(tm_row + C_A, P.xp);
-    tmem_wait_st();
+    const bool b0 = prep_node(d, omega, p.force,
+                              (count > 0 && p.force) ? __ldg(p.force + T.y) : 0.f, a1, r, P);
+    bad = act && b0;
   }
 
   for (int it = 0; it < count; ++it) {
     const int x = T.x0 + r;
     const bool active = x < nx;
 
-    // ---- layer 1 (its operand rows were written before the loop or at the
-    // end of the previous tile)
+    // ---- layer 1 (its operand rows were written before the loop or during
+    // the previous tile's layer 3)
+    fence_proxy_async();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
-      mma_bf16_ta(acc, a_op, dw1, ID64, 0);
+      mma_bf16(tm_wg, da1, db1, ID64, 0);
       mma_commit(bar);
     }
 
@@ -424,57 +424,59 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (nact) pull_node(in, plane, nx, ny, N, N.x0 + r, dn);
     const float fxn = (more && p.force) ? __ldg(p.force + N.y) : 0.f;
 
-    // ---- layer 1 epilogue: h1 -> A operand; layer 2
+    // ---- layer 1 epilogue: h1 -> operand of layer 2; layer 2
     if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     phase ^= 1;
     fence_after_sync();
-    hidden_epilogue(tm_row);
-    tmem_wait_st();
+    hidden_epilogue(tm_row, a23, r);
+    fence_proxy_async();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
-      for (int s = 0; s < KH / 16; ++s)
-        mma_bf16_ta(acc, a_op + 8 * s, smem_desc(sw2 + 256 * s, 128, 16 * KH), ID64, s > 0);
-      mma_bf16_ta(acc, ones, dbb2, ID64, 1);
+      for (int s = 0; s < K2 / 16; ++s)
+        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+                 smem_desc(sw2 + 256 * s, 128, 16 * K2), ID64, s > 0);
       mma_commit(bar);
     }
 
-    // ---- layer 2 epilogue: h2 -> A operand; layer 3
+    // ---- layer 2 epilogue: h2 -> operand of layer 3; layer 3
     if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     phase ^= 1;
     fence_after_sync();
-    hidden_epilogue(tm_row);
-    tmem_wait_st();
+    hidden_epilogue(tm_row, a23, r);
+    fence_proxy_async();
     fence_before_sync();
     named_barrier(bar_id, WG_THREADS);
     if (leader) {
       fence_after_sync();
 #pragma unroll
-      for (int s = 0; s < KH / 16; ++s)
-        mma_bf16_ta(acc, a_op + 8 * s, smem_desc(sw3 + 256 * s, 128, 16 * KH), ID16, s > 0);
-      mma_bf16_ta(acc, ones, dbb3, ID16, 1);
+      for (int s = 0; s < K2 / 16; ++s)
+        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
+                 smem_desc(sw3 + 256 * s, 128, 16 * K2), ID16, s > 0);
       mma_commit(bar);
     }
 
-    // ---- the next tile's per-node work while layer 3 runs
+    // ---- the next tile's per-node work while layer 3 runs (layer 1 of this
+    // tile has read a1)
     NodePrep Pn;
-    prep_node(dn, omega, p.force, fxn, Pn);
-    bad |= nact && Pn.bad;
+    {
+      const bool bn = prep_node(dn, omega, p.force, fxn, a1, r, Pn);
+      bad |= nact && bn;
+    }
 
-    // ---- layer 3 epilogue: projection, update, store; the next tile's x
+    // ---- layer 3 epilogue: projection, update, store
     if (leader) fail = !wait_gemm(bar, phase, wait_limit);
     if (barrier_any(bar_id, WG_THREADS, fail)) break;
     phase ^= 1;
     fence_after_sync();
     {
       uint32_t ov[16];
-      tmem_ld16(tm_row + C_ACC, ov);
+      tmem_ld16(tm_row, ov);
       tmem_wait_ld();
-      if (more) tmem_st8(tm_row + C_A, Pn.xp);  // layer 3 has read the A operand
       if (active) {
         float f[Q];
         finish_node(ov, P, f);
@@ -482,7 +484,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int i = 0; i < Q; ++i) ob[(size_t)i * plane] = f[i];
       }
-      tmem_wait_st();
     }
     P = Pn;
     T = N;

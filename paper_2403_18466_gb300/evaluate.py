@@ -26,7 +26,7 @@ import numpy as np
 import torch
 
 from . import data as data_mod
-from . import lbm
+from . import inputs, lbm
 from .train import train
 
 
@@ -37,17 +37,24 @@ def _spectrum_error(E, Eref, kmax):
 
 def evaluate(dns=2048, cg=8, tau=0.503, force_amp=1e-5, force_mode=4, epochs=200, lr=1e-3,
              trajectories=32, unroll=16, steps=2000, every=250, spinup=5000, seed=4,
-             precision="bf16", smag_cs=0.1, filter="box", device="cuda", verbose=True):
+             precision="bf16", smag_cs=0.1, filter="box", device="cuda", verbose=True,
+             dns_eval=None, theta=None):
+    """dns_eval: size of the evaluation DNS (default: the training DNS size);
+    the learned collision is local, so a model trained on the dns -> dns/cg
+    pair applies to any dns_eval -> dns_eval/cg pair at the same tau and cg.
+    theta: trained weights to use instead of training here."""
     t0 = time.perf_counter()
-    ds = data_mod.generate(n=dns, cg=cg, tau=tau, force_amp=force_amp, force_mode=force_mode,
-                           trajectories=trajectories, unroll=unroll, spinup=spinup, seed=seed,
-                           filter=filter, device=device)
-    theta, hist = train(ds, epochs=epochs, lr=lr, verbose=False, precision=precision)
+    hist = [float("nan")]
+    if theta is None:
+        ds = data_mod.generate(n=dns, cg=cg, tau=tau, force_amp=force_amp,
+                               force_mode=force_mode, trajectories=trajectories, unroll=unroll,
+                               spinup=spinup, seed=seed, filter=filter, device=device)
+        theta, hist = train(ds, epochs=epochs, lr=lr, verbose=False, precision=precision)
     t_train = time.perf_counter() - t0
 
     # a fresh DNS state beyond the training snapshots, and its filtered populations
-    from . import inputs
-    n, N = dns, dns // cg
+    n = dns_eval or dns
+    N = n // cg
     rho, ux, uy = inputs.random_velocity_field(n, n, seed=seed + 100, k0=8.0, urms=0.02)
     fine = lbm.Lattice(n, n, 1, tau=tau, force_amp=force_amp, force_mode=force_mode,
                        device=device)
@@ -59,12 +66,13 @@ def evaluate(dns=2048, cg=8, tau=0.503, force_amp=1e-5, force_mode=4, epochs=200
     runs = {}
     w = lbm.weights_struct(theta.contiguous())
     kind_learned = "mlp_bf16" if precision == "bf16" else "mlp_f32"
+    tau_les, force_les = data_mod.rescaled_tau(tau, cg), cg * force_amp
     for name, kind in (("bgk", "bgk"), ("smag", "smag"), ("learned", kind_learned)):
-        lat = lbm.Lattice(N, N, 1, tau=ds.tau_les, smag_cs=smag_cs, force_amp=ds.force_les,
+        lat = lbm.Lattice(N, N, 1, tau=tau_les, smag_cs=smag_cs, force_amp=force_les,
                           force_mode=force_mode, device=device)
         lat.set_state(f0)
         runs[name] = (lat, kind)
-    ref = lbm.Lattice(N, N, 1, tau=ds.tau_les, device=device)  # holds the filtered DNS state
+    ref = lbm.Lattice(N, N, 1, tau=tau_les, device=device)  # holds the filtered DNS state
     kmax = N // 2
     rmax = N // 4
     out = {"steps": [], "spectrum_error": {k: [] for k in runs}, "velocity_error": {k: [] for k in runs},
@@ -111,6 +119,9 @@ def evaluate(dns=2048, cg=8, tau=0.503, force_amp=1e-5, force_mode=4, epochs=200
         out["status"][name] = lbm.lbm_strerror(lat.status())
     out["train"] = {"epochs": epochs, "first_loss": hist[0], "last_loss": hist[-1],
                     "seconds": round(t_train, 1)}
+    out["pair"] = {"dns": n, "les": N, "cg": cg, "tau_les": tau_les, "force_les": force_les}
+    if fine.status() != lbm.LBM_OK:
+        out["dns_status"] = lbm.lbm_strerror(fine.status())
     out["wall_s"] = round(time.perf_counter() - t0, 1)
     out["final_spectra"] = {k: v.tolist() for k, v in E_last.items()}
     out["final_S2"] = {k: v[1].tolist() for k, v in S_last.items()}
@@ -128,11 +139,15 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--filter", default="box", choices=["box", "subsample"])
     ap.add_argument("--out", default=None, help="write the full record as JSON")
+    ap.add_argument("--dns-eval", type=int, default=None, help="evaluation DNS size")
+    ap.add_argument("--weights", default=None, help="trained weights (torch.save), skip training")
     args = ap.parse_args()
+    theta = inputs.load_weights(args.weights, "cuda") if args.weights else None
     res = evaluate(dns=args.dns, cg=args.cg, epochs=args.epochs, lr=args.lr, steps=args.steps,
-                   every=args.every, precision=args.precision, filter=args.filter)
+                   every=args.every, precision=args.precision, filter=args.filter,
+                   dns_eval=args.dns_eval, theta=theta)
     summary = {k: res[k] for k in ("steps", "spectrum_error", "velocity_error", "status",
-                                   "unstable_at", "train", "wall_s")}
+                                   "unstable_at", "train", "wall_s", "pair")}
     print(json.dumps(summary))
     if args.out:
         with open(args.out, "w") as fh:

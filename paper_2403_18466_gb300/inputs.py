@@ -165,3 +165,19 @@ def noise(shape, seed: int, scale: float):
     """Uniform noise in [-scale, scale] (float64), seeded."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return scale * rng.uniform(-1.0, 1.0, size=shape)
+
+
+def save_weights(theta, path):
+    """Write a packed weight vector (torch tensor or array) as float32 .npy."""
+    a = theta.detach().cpu().numpy() if hasattr(theta, "detach") else np.asarray(theta)
+    np.save(path, a.astype(np.float32))
+
+
+def load_weights(path, device=None):
+    """Read a packed weight vector written by save_weights; a CUDA float32
+    tensor if `device` is given, else a float64 numpy array."""
+    a = np.load(path).astype(np.float64)
+    if device is None:
+        return a
+    import torch
+    return torch.tensor(a, dtype=torch.float32, device=device)

@@ -23,9 +23,12 @@ from . import inputs, lbm
 
 def run(n=1024, kind="smag", steps=10000, every=1000, tau=0.51, smag_cs=0.1, force_amp=1e-5,
         force_mode=4, seed=1, k0=8.0, urms=0.02, theta=None, rmax=None, kmax=None,
-        device="cuda"):
+        device="cuda", stop_on_unstable=False):
     """Returns dict with step list, spectra [m, kmax+1], structure functions
-    [m, 6, rmax] (numpy), the wall time, and the lattice status."""
+    [m, 6, rmax] (numpy), the wall time, and the lattice status.  With
+    stop_on_unstable, the run ends at the first record whose status is not OK
+    (|u| >= 0.4 or non-finite somewhere since the previous record) and
+    "unstable_at" gives that record's step (None if it stayed stable)."""
     rho, ux, uy = inputs.random_velocity_field(n, n, seed=seed, k0=k0, urms=urms)
     lat = lbm.Lattice(n, n, 1, tau=tau, smag_cs=smag_cs, force_amp=force_amp,
                       force_mode=force_mode, device=device)
@@ -37,18 +40,58 @@ def run(n=1024, kind="smag", steps=10000, every=1000, tau=0.51, smag_cs=0.1, for
     steps_rec, spectra, sfs = [], [], []
     t0 = time.perf_counter()
     done = 0
+    unstable_at = None
+    step_time = 0.0
     while done < steps:
         k = min(every, steps - done)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         lat.step(k, kind, w)
+        b.record()
         done += k
+        if stop_on_unstable and lat.status() != lbm.LBM_OK:
+            unstable_at = done
+            break
+        step_time += a.elapsed_time(b) * 1e-3
         spectra.append(lat.energy_spectrum(kmax))
         sfs.append(lat.structure_functions(rmax))
         steps_rec.append(done)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    return {"steps": steps_rec, "E": torch.stack(spectra).cpu().numpy(),
-            "S": torch.stack(sfs).cpu().numpy(), "wall_s": wall,
-            "mlups": n * n * steps / wall / 1e6, "status": lbm.lbm_strerror(lat.status())}
+    stepped = steps_rec[-1] if steps_rec else 0
+    return {"steps": steps_rec,
+            "E": torch.stack(spectra).cpu().numpy() if spectra else np.zeros((0, kmax + 1)),
+            "S": torch.stack(sfs).cpu().numpy() if sfs else np.zeros((0, 6, rmax)),
+            "wall_s": wall, "unstable_at": unstable_at,
+            "mlups": n * n * stepped / step_time / 1e6 if step_time > 0 else float("nan"),
+            "status": lbm.lbm_strerror(lat.status())}
+
+
+def long_comparison(theta, n=8192, steps=100000, every=1000, tau=0.500375, smag_cs=0.1,
+                    force_amp=1e-5, force_mode=4, seed=5, rmax=256, device="cuda"):
+    """The long learned-collision LES against the Smagorinsky LES from the same
+    initial field: each run until `steps` or its first unstable record.
+    Returns, per kind, the records' steps and energies, the spectrum and
+    S^p(r) (p = 2..6, r = 1..rmax) at the last stable record and every tenth
+    record, the ESS exponents of the time-averaged S^p, the unstable step and
+    the throughput of the stepping."""
+    out = {}
+    for kind in ("mlp_bf16", "smag"):
+        res = run(n=n, kind=kind, steps=steps, every=every, tau=tau, smag_cs=smag_cs,
+                  force_amp=force_amp, force_mode=force_mode, seed=seed,
+                  theta=theta if kind == "mlp_bf16" else None, rmax=rmax, device=device,
+                  stop_on_unstable=True)
+        E, S = res["E"], res["S"]
+        keep = list(range(0, len(res["steps"]), 10)) + ([len(res["steps"]) - 1] if len(res["steps"]) else [])
+        out[kind] = {
+            "steps": res["steps"], "energy": [float(e.sum()) for e in E],
+            "unstable_at": res["unstable_at"], "mlups": round(res["mlups"], 1),
+            "wall_s": round(res["wall_s"], 1),
+            "spectra": {int(res["steps"][i]): E[i].tolist() for i in sorted(set(keep))},
+            "S": {int(res["steps"][i]): S[i][1:].tolist() for i in sorted(set(keep))},
+            "ess": [float(v) for v in ess_exponents(S.mean(0))] if len(S) else None,
+        }
+    return out
 
 
 def ess_exponents(S, s3_range=None):
@@ -72,6 +115,9 @@ def ess_exponents(S, s3_range=None):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--compare", action="store_true",
+                    help="learned (--weights) against Smagorinsky, until unstable")
+    ap.add_argument("--out", default=None, help="write the comparison record as JSON")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--kind", default="smag", choices=["bgk", "smag", "mlp_bf16", "mlp_f32"])
     ap.add_argument("--steps", type=int, default=10000)
@@ -81,7 +127,17 @@ def main():
     args = ap.parse_args()
     theta = None
     if args.weights:
-        theta = torch.load(args.weights).to("cuda", torch.float32)
+        theta = inputs.load_weights(args.weights, "cuda")
+    if args.compare:
+        rec = long_comparison(theta, n=args.n, steps=args.steps, every=args.every, tau=args.tau)
+        print(json.dumps({k: {f: v[f] for f in ("unstable_at", "mlups", "wall_s", "ess")}
+                          | {"records": len(v["steps"]),
+                             "energy_last": v["energy"][-1] if v["energy"] else None}
+                          for k, v in rec.items()}))
+        if args.out:
+            with open(args.out, "w") as fh:
+                json.dump(rec, fh)
+        return
     res = run(n=args.n, kind=args.kind, steps=args.steps, every=args.every, tau=args.tau,
               theta=theta)
     S_mean = res["S"].mean(0)

@@ -89,7 +89,7 @@ def main():
     ap.add_argument("--filter", default="box", choices=["box", "subsample"])
     ap.add_argument("--subset", type=int, default=0, help="|S| of the subset loss (paper: 512)")
     ap.add_argument("--loss", default="velocity", choices=["velocity", "population"])
-    ap.add_argument("--save", default=None, help="write the trained weights (torch.save)")
+    ap.add_argument("--save", default=None, help="write the trained weights (.npy: float32 packed vector)")
     args = ap.parse_args()
     ds = data_mod.generate(n=args.dns, cg=args.cg, trajectories=args.trajectories,
                            unroll=args.unroll, filter=args.filter)
@@ -101,7 +101,7 @@ def main():
     print(json.dumps({"trained_loss": learned, "first_epoch_loss": hist[0],
                       "baseline_loss": base}), flush=True)
     if args.save:
-        torch.save(theta.cpu(), args.save)
+        inputs.save_weights(theta, args.save)
 
 
 if __name__ == "__main__":
