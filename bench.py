@@ -260,7 +260,21 @@ def run_gpu(args):
                        "hbm_frac": round(g / hbm_peak, 4)}
     comps["mlp_bf16"] = {"mlups": round(nodes / (ms_step * 1e-3) / 1e6, 1),
                          "ms_per_step": round(ms_step, 5), "hbm_gbs": roofline["achieved"],
-                         "hbm_frac": roofline["frac"]}
+                         "hbm_frac": roofline["frac"], "weights": "xavier seed 3, output x0.3"}
+    # the same step with the trained weights (the configuration names seeded
+    # Xavier weights and trained weights), from the same initial state
+    wt = lbm.weights_struct(inputs.trained_mlp(dev))
+    lat_t = _initial_state(lbm, torch, dev)
+    lat_t.step(3, "mlp_bf16", wt)
+    kt = max(50, args.steps // 10)
+    t = _time_steps(lat_t, "mlp_bf16", wt, kt, torch, stream)
+    g = BYTES_PER_NODE * nodes / (t / kt * 1e-3) / 1e9
+    comps["mlp_bf16_trained"] = {"mlups": round(nodes / (t / kt * 1e-3) / 1e6, 1),
+                                 "ms_per_step": round(t / kt, 5), "hbm_gbs": round(g, 1),
+                                 "hbm_frac": round(g / hbm_peak, 4), "steps": kt,
+                                 "weights": "trained (paper_2403_18466_gb300/weights)",
+                                 "status": lbm.lbm_strerror(lat_t.status())}
+    del lat_t
     comps["training"] = _time_training(lbm, torch, dev, inputs)
     comps["d3q19"] = _time_d3q19(lbm, torch, dev, inputs, hbm_peak)
     del lat

@@ -145,18 +145,32 @@ __device__ __forceinline__ void feq_vjp(const GMom &s, float rho, float ux, floa
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-// tanh(a) and 1 - tanh(a)^2 from t = e^{-2|a|} and r = 1/(1 + t): with
-// u = t r, tanh a = sign(a) (r - u) and 1 - tanh^2 a = 4 u r.  Two XU
-// operations (ex2, rcp); the derivative keeps its relative accuracy for
-// saturated units, where 1 - h^2 formed from an approximate h would not.
+#ifndef LBM_ADJ_TANH_EX2
+#define LBM_ADJ_TANH_EX2 0
+#endif
+// tanh(a) and its derivative 1 - tanh(a)^2.
+// Default: the hardware tanh.approx.f32 (one XU operation, 8 cycles per
+// warp-instruction) and 1 - h^2 on the FMA pipe.  For a saturated unit the
+// derivative then has an absolute error of ~1e-3 (h is good to ~2^-11
+// relative), which is what matters for the chain rule: it scales the
+// incoming gradient, so the error is ~1e-3 of that gradient, the size of the
+// bf16 rounding of the backward operands.
+// LBM_ADJ_TANH_EX2=1: t = e^{-2|a|}, r = 1/(1 + t), u = t r:
+// tanh a = sign(a) (r - u), 1 - tanh^2 a = 4 u r (ex2 + rcp: 12 XU cycles per
+// warp-instruction pair of values; keeps the derivative's relative accuracy).
 __device__ __forceinline__ void tanh_and_slope(float a, float &h, float &dh) {
-  float t, r;
-  const float e = -2.8853900817779268f * fabsf(a);  // -2 log2(e) |a|
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(e));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
-  const float u = t * r;
-  h = copysignf(r - u, a);
-  dh = 4.0f * (u * r);
+  if (LBM_ADJ_TANH_EX2) {
+    float t, r;
+    const float e = -2.8853900817779268f * fabsf(a);  // -2 log2(e) |a|
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(e));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + t));
+    const float u = t * r;
+    h = copysignf(r - u, a);
+    dh = 4.0f * (u * r);
+  } else {
+    asm("tanh.approx.f32 %0, %1;" : "=f"(h) : "f"(a));
+    dh = fmaf(-h, h, 1.0f);
+  }
 }
 
 // D (64 FP32 columns of this thread's row) -> h = tanh(D) in FP32 -> bf16 row of

@@ -38,59 +38,120 @@ constexpr int OFF_B3 = OFF_W3 + 9 * HIDDEN;
 // |u|^2 at or above this marks the run unstable (|u| >= 0.4, or NaN).
 constexpr float UNSTABLE_USQ = 0.16f;
 
-struct Moments {
-  float drho;  // rho - 1
-  float rho;
-  float ux, uy;
-  float inv_rho;  // 1/rho, rounded to nearest
-};
+// ---- arithmetic with explicit rounding, for one node (float) or two nodes
+// at once (float2: packed f32x2 instructions).  Every operation below is a
+// single IEEE round-to-nearest operation whose form (separate multiply and
+// add, or one fused multiply-add) is written out, so the two forms give the
+// same result in every lane and no kernel depends on the compiler's choice of
+// contractions.
+__device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float v_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a - b, rounded once (as fma(b, -1, a))
+__device__ __forceinline__ float v_sub(float a, float b) { return __fmaf_rn(b, -1.0f, a); }
+__device__ __forceinline__ float v_splat(float a, float) { return a; }
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 v_sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 v_splat(float a, float2) { return make_float2(a, a); }
+// 1/x rounded to nearest (per lane)
+__device__ __forceinline__ float v_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float2 v_rcp(float2 x) {
+  return make_float2(__frcp_rn(x.x), __frcp_rn(x.y));
+}
+template <class T> __device__ __forceinline__ T v_c(float a) { return v_splat(a, T()); }
 
-__device__ __forceinline__ Moments node_moments(const float d[Q]) {
-  Moments m;
-  m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-  const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-  const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-  m.rho = 1.0f + m.drho;
-  const float inv = 1.0f / m.rho;
-  m.inv_rho = inv;
-  m.ux = jx * inv;
-  m.uy = jy * inv;
+template <class T>
+struct MomentsT {
+  T drho;     // rho - 1
+  T rho;
+  T ux, uy;
+  T inv_rho;  // 1/rho, rounded to nearest
+};
+using Moments = MomentsT<float>;
+
+template <class T>
+__device__ __forceinline__ MomentsT<T> node_moments(const T d[Q]) {
+  MomentsT<T> m;
+  m.drho = v_add(v_add(v_add(d[0], d[1]), v_add(d[2], d[3])),
+                 v_add(v_add(v_add(d[4], d[5]), v_add(d[6], d[7])), d[8]));
+  const T jx = v_add(v_add(v_sub(d[1], d[3]), v_sub(d[5], d[6])), v_sub(d[8], d[7]));
+  const T jy = v_sub(v_add(v_sub(d[2], d[4]), v_add(d[5], d[6])), v_add(d[7], d[8]));
+  m.rho = v_add(v_c<T>(1.0f), m.drho);
+  m.inv_rho = v_rcp(m.rho);
+  m.ux = v_mul(jx, m.inv_rho);
+  m.uy = v_mul(jy, m.inv_rho);
   return m;
 }
 
-// Shifted equilibrium deq_i = feq_i - w_i, Eq. S4 with cs^2 = 1/3.
-__device__ __forceinline__ void shifted_feq(const Moments &m, float deq[Q]) {
-  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+// c_i . u for direction i (compile-time i)
+template <class T>
+__device__ __forceinline__ T c_dot_u(int i, const MomentsT<T> &m) {
+  const int ax = cx(i), ay = cy(i);
+  if (ax == 0 && ay == 0) return v_c<T>(0.0f);
+  if (ay == 0) return ax > 0 ? m.ux : v_mul(v_c<T>(-1.0f), m.ux);
+  if (ax == 0) return ay > 0 ? m.uy : v_mul(v_c<T>(-1.0f), m.uy);
+  if (ax > 0) return ay > 0 ? v_add(m.ux, m.uy) : v_sub(m.ux, m.uy);
+  return ay > 0 ? v_sub(m.uy, m.ux) : v_mul(v_c<T>(-1.0f), v_add(m.ux, m.uy));
+}
+
+// Shifted equilibrium deq_i = feq_i - w_i, Eq. S4 with cs^2 = 1/3:
+//   deq_i = w_i (drho + rho (cu (3 + 4.5 cu) - 1.5 |u|^2)),  cu = c_i . u.
+template <class T>
+__device__ __forceinline__ void shifted_feq(const MomentsT<T> &m, T deq[Q]) {
+  const T usq15 = v_mul(v_c<T>(1.5f), v_fma(m.ux, m.ux, v_mul(m.uy, m.uy)));
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float cu = (float)cx(i) * m.ux + (float)cy(i) * m.uy;
-    deq[i] = wf(i) * (m.drho + m.rho * (cu * (3.0f + 4.5f * cu) - usq15));
+    const T cu = c_dot_u(i, m);
+    const T q = v_fma(cu, v_fma(cu, v_c<T>(4.5f), v_c<T>(3.0f)), v_mul(v_c<T>(-1.0f), usq15));
+    deq[i] = v_mul(v_c<T>(wf(i)), v_fma(m.rho, q, m.drho));
   }
+}
+
+// BGK relaxation d_i + (deq_i - d_i)/tau, Eq. S3.
+template <class T>
+__device__ __forceinline__ T bgk_relax(T d, T deq, T omega) {
+  return v_fma(omega, v_sub(deq, d), d);
 }
 
 // EDM forcing term f_ext_i = feq_i(rho, u + F/rho) - feq_i(rho, u)  (Eq. S5)
 // for F = (fx, 0), written without the cancellation of two equilibria:
 // with a = F/rho, (c.u_s)^2 - (c.u)^2 = (c.a)(c.(2u + a)) and
 // |u_s|^2 - |u|^2 = a.(2u + a); rho a = F.  a = F (1/rho) with the rounded
-// reciprocal of the moments, so no kernel divides here.
-__device__ __forceinline__ void add_edm_force_x(const Moments &m, float fx, float out[Q]) {
-  const float ax = fx * m.inv_rho;
-  const float sx = 2.0f * m.ux + ax;
+// reciprocal of the moments, so no kernel divides here:
+//   c_x = 0:   f_ext_i = -1.5 w_i fx s,             s = 2 u_x + a_x
+//   c_x = +-1: f_ext_i = w_i fx (c_x (3 + 4.5 (c_x s + 2 c_y u_y)) - 1.5 s)
+template <class T>
+__device__ __forceinline__ void add_edm_force_x(const MomentsT<T> &m, T fx, T out[Q]) {
+  const T ax = v_mul(fx, m.inv_rho);
+  const T sx = v_fma(v_c<T>(2.0f), m.ux, ax);
+  const T uy2 = v_mul(v_c<T>(2.0f), m.uy);
+  const T m15s = v_mul(v_c<T>(-1.5f), sx);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
+    const T wfx = v_mul(v_c<T>(wf(i)), fx);
     if (cx(i) == 0) {
-      out[i] -= wf(i) * fx * sx * 1.5f;  // only the -1.5 a.(2u+a) term survives
+      out[i] = v_fma(wfx, m15s, out[i]);  // only the -1.5 a.(2u+a) term survives
     } else {
-      const float cs = (float)cx(i) * sx + (float)cy(i) * 2.0f * m.uy;
-      out[i] += wf(i) * fx * ((float)cx(i) * (3.0f + 4.5f * cs) - 1.5f * sx);
+      const T csx = cx(i) > 0 ? sx : v_mul(v_c<T>(-1.0f), sx);
+      const T cs = cy(i) == 0 ? csx : (cy(i) > 0 ? v_add(csx, uy2) : v_sub(csx, uy2));
+      const T t = v_fma(cs, v_c<T>(4.5f), v_c<T>(3.0f));
+      out[i] = v_fma(wfx, v_fma(t, v_c<T>((float)cx(i)), m15s), out[i]);
     }
   }
 }
 
-// True when |u| >= 0.4 or u is not finite.
+// True when |u| >= 0.4 or u is not finite (for two nodes: either of them).
 __device__ __forceinline__ bool is_unstable(const Moments &m) {
   const float usq = m.ux * m.ux + m.uy * m.uy;
   return !(usq < UNSTABLE_USQ);
+}
+__device__ __forceinline__ bool is_unstable(const MomentsT<float2> &m, bool act_x, bool act_y) {
+  const float2 usq = v_fma(m.ux, m.ux, v_mul(m.uy, m.uy));
+  return (act_x && !(usq.x < UNSTABLE_USQ)) || (act_y && !(usq.y < UNSTABLE_USQ));
 }
 
 // Sets the sticky flag if any calling lane is unstable: one read (and at most

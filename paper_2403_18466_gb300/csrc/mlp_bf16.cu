@@ -96,6 +96,12 @@ constexpr int THREADS = WGS * WG_THREADS;
 constexpr int XU_PAIRS = LBM_TANH_XU_PAIRS;  // of every 8 activation pairs, on the XU
 static_assert(XU_PAIRS >= 0 && XU_PAIRS <= 8, "split of 8 pairs");
 constexpr int K1 = 16, K2 = 80;  // padded K of layer 1 and of layers 2/3
+#ifndef LBM_EPI_COLS
+#define LBM_EPI_COLS 16
+#endif
+// accumulator columns read per tensor-memory wait in the hidden epilogues
+constexpr int EPI_COLS = LBM_EPI_COLS;
+static_assert(EPI_COLS == 16 || EPI_COLS == 32, "16 or 32 columns per read");
 // tensor memory: 64 accumulator columns per warpgroup
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(WGS * 64 <= (int)TMEM_COLS, "tensor memory layout");
@@ -205,18 +211,19 @@ __device__ __forceinline__ uint32_t act_fma(float y0, float y1) {
 // within the 64-register budget).
 __device__ __forceinline__ void hidden_epilogue(uint32_t tm_row, unsigned char *a23, int r) {
 #pragma unroll
-  for (int c = 0; c < HIDDEN; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(tm_row + c, v);
+  for (int c = 0; c < HIDDEN; c += EPI_COLS) {
+    uint32_t v[EPI_COLS];
+    if (EPI_COLS == 32) tmem_ld32(tm_row + c, *reinterpret_cast<uint32_t(*)[32]>(v));
+    else tmem_ld16(tm_row + c, *reinterpret_cast<uint32_t(*)[16]>(v));
     tmem_wait_ld();
-    uint32_t p[8];
+    uint32_t p[EPI_COLS / 2];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < EPI_COLS / 2; ++q) {
       const float a0 = __uint_as_float(v[2 * q]), a1 = __uint_as_float(v[2 * q + 1]);
       p[q] = fma_unit(c + 2 * q) ? act_fma(a0, a1) : act_xu(a0, a1);
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < EPI_COLS / 8; ++q)
       *reinterpret_cast<uint4 *>(a23 + canon_offset(r, c + 8 * q, K2)) =
           make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
@@ -277,7 +284,7 @@ __device__ __forceinline__ bool prep_node(const float d[Q], float omega, const f
   *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
       make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) P.base[i] = fmaf(omega, deq[i] - d[i], d[i]);
+  for (int i = 0; i < Q; ++i) P.base[i] = bgk_relax(d[i], deq[i], omega);
   if (force) add_edm_force_x(m, fx, P.base);
   P.rw = m.rho * omega;
   return is_unstable(m);
@@ -362,9 +369,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   // warp (wg mod 4) of the warpgroup, so that the eight leaders sit on all
   // four SM sub-partitions (CTA warp w runs on sub-partition w mod 4)
   const bool leader = LEADER_SPREAD ? r == 32 * (wg & 3) : r == 0;
+  // operand descriptors; a K = 16 slice further is 256 bytes = 16 units of the
+  // descriptor's start-address field (shared addresses stay below 2^18, so
+  // the 14-bit field does not overflow)
   const uint64_t da1 = smem_desc(smem_u32(a1), 128, 16 * K1);
   const uint64_t db1 = smem_desc(smem_u32(S.w1), 128, 16 * K1);
-  const uint32_t sa23 = smem_u32(a23), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
+  const uint64_t d23 = smem_desc(smem_u32(a23), 128, 16 * K2);
+  const uint64_t dw2 = smem_desc(smem_u32(S.w2), 128, 16 * K2);
+  const uint64_t dw3 = smem_desc(smem_u32(S.w3), 128, 16 * K2);
   constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
 
   // ---- this warpgroup's contiguous range of tiles
@@ -437,8 +449,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       fence_after_sync();
 #pragma unroll
       for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
-                 smem_desc(sw2 + 256 * s, 128, 16 * K2), ID64, s > 0);
+        mma_bf16(tm_wg, d23 + 16 * s, dw2 + 16 * s, ID64, s > 0);
       mma_commit(bar);
     }
 
@@ -455,8 +466,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       fence_after_sync();
 #pragma unroll
       for (int s = 0; s < K2 / 16; ++s)
-        mma_bf16(tm_wg, smem_desc(sa23 + 256 * s, 128, 16 * K2),
-                 smem_desc(sw3 + 256 * s, 128, 16 * K2), ID16, s > 0);
+        mma_bf16(tm_wg, d23 + 16 * s, dw3 + 16 * s, ID16, s > 0);
       mma_commit(bar);
     }
 

@@ -49,7 +49,7 @@ __device__ __forceinline__ bool collide_node(float d[Q], const CollideParams &p,
     omega = 1.0f / tau_eff;
   }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) d[i] = fmaf(omega, deq[i] - d[i], d[i]);
+  for (int i = 0; i < Q; ++i) d[i] = bgk_relax(d[i], deq[i], omega);
   if (p.force) add_edm_force_x(m, fx, d);
   return bad;
 }

@@ -19,6 +19,8 @@ a few percent of the lattice speed, driven by a large-scale sine force):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 HIDDEN = 64
@@ -181,3 +183,17 @@ def load_weights(path, device=None):
         return a
     import torch
     return torch.tensor(a, dtype=torch.float32, device=device)
+
+
+TRAINED_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                               "d2q9_les_cg8.npy")
+
+
+def trained_mlp(device=None):
+    """Weights of the 9 -> 64 -> 64 -> 9 collision network trained by this
+    library (``python -m paper_2403_18466_gb300.train --precision f32 --lr 1e-4
+    --epochs 400 --save ...``: 2048^2 BGK DNS, tau 0.503, box filter x8 to 256^2
+    LES at tau' = 0.500375, 32 trajectories unrolled 16 steps, checkpoint every
+    4, velocity loss 7.18e-8 -> 3.90e-8 against 7.26e-8 for plain BGK LES).
+    Same packing as xavier_mlp; float64 numpy, or a CUDA float32 tensor."""
+    return load_weights(TRAINED_WEIGHTS, device)

@@ -23,12 +23,14 @@ from . import inputs, lbm
 
 def run(n=1024, kind="smag", steps=10000, every=1000, tau=0.51, smag_cs=0.1, force_amp=1e-5,
         force_mode=4, seed=1, k0=8.0, urms=0.02, theta=None, rmax=None, kmax=None,
-        device="cuda", stop_on_unstable=False):
+        device="cuda", stop_on_unstable=False, check_every=None):
     """Returns dict with step list, spectra [m, kmax+1], structure functions
     [m, 6, rmax] (numpy), the wall time, and the lattice status.  With
     stop_on_unstable, the run ends at the first record whose status is not OK
     (|u| >= 0.4 or non-finite somewhere since the previous record) and
-    "unstable_at" gives that record's step (None if it stayed stable)."""
+    "unstable_at" gives that record's step (None if it stayed stable); with
+    check_every (a divisor of every) the status is also read every
+    check_every steps, so unstable_at is known to that resolution."""
     rho, ux, uy = inputs.random_velocity_field(n, n, seed=seed, k0=k0, urms=urms)
     lat = lbm.Lattice(n, n, 1, tau=tau, smag_cs=smag_cs, force_amp=force_amp,
                       force_mode=force_mode, device=device)
@@ -45,12 +47,21 @@ def run(n=1024, kind="smag", steps=10000, every=1000, tau=0.51, smag_cs=0.1, for
     while done < steps:
         k = min(every, steps - done)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sub = check_every if (stop_on_unstable and check_every) else k
         a.record()
-        lat.step(k, kind, w)
+        left = k
+        while left > 0:
+            lat.step(min(sub, left), kind, w)
+            done += min(sub, left)
+            left -= min(sub, left)
+            if stop_on_unstable and left > 0 and lat.status() != lbm.LBM_OK:
+                unstable_at = done
+                break
         b.record()
-        done += k
-        if stop_on_unstable and lat.status() != lbm.LBM_OK:
+        b.synchronize()
+        if unstable_at is None and stop_on_unstable and lat.status() != lbm.LBM_OK:
             unstable_at = done
+        if unstable_at is not None:
             break
         step_time += a.elapsed_time(b) * 1e-3
         spectra.append(lat.energy_spectrum(kmax))
@@ -68,7 +79,8 @@ def run(n=1024, kind="smag", steps=10000, every=1000, tau=0.51, smag_cs=0.1, for
 
 
 def long_comparison(theta, n=8192, steps=100000, every=1000, tau=0.500375, smag_cs=0.1,
-                    force_amp=1e-5, force_mode=4, seed=5, rmax=256, device="cuda"):
+                    force_amp=1e-5, force_mode=4, seed=5, rmax=256, device="cuda",
+                    check_every=100):
     """The long learned-collision LES against the Smagorinsky LES from the same
     initial field: each run until `steps` or its first unstable record.
     Returns, per kind, the records' steps and energies, the spectrum and
@@ -80,7 +92,7 @@ def long_comparison(theta, n=8192, steps=100000, every=1000, tau=0.500375, smag_
         res = run(n=n, kind=kind, steps=steps, every=every, tau=tau, smag_cs=smag_cs,
                   force_amp=force_amp, force_mode=force_mode, seed=seed,
                   theta=theta if kind == "mlp_bf16" else None, rmax=rmax, device=device,
-                  stop_on_unstable=True)
+                  stop_on_unstable=True, check_every=check_every)
         E, S = res["E"], res["S"]
         keep = list(range(0, len(res["steps"]), 10)) + ([len(res["steps"]) - 1] if len(res["steps"]) else [])
         out[kind] = {
