@@ -118,28 +118,28 @@ __device__ __forceinline__ T bgk_relax(T d, T deq, T omega) {
 }
 
 // EDM forcing term f_ext_i = feq_i(rho, u + F/rho) - feq_i(rho, u)  (Eq. S5)
-// for F = (fx, 0), written without the cancellation of two equilibria:
-// with a = F/rho, (c.u_s)^2 - (c.u)^2 = (c.a)(c.(2u + a)) and
-// |u_s|^2 - |u|^2 = a.(2u + a); rho a = F.  a = F (1/rho) with the rounded
-// reciprocal of the moments, so no kernel divides here:
-//   c_x = 0:   f_ext_i = -1.5 w_i fx s,             s = 2 u_x + a_x
-//   c_x = +-1: f_ext_i = w_i fx (c_x (3 + 4.5 (c_x s + 2 c_y u_y)) - 1.5 s)
+// for F = (fx, 0), written without the cancellation of two equilibria.  With
+// a = F/rho (a = F (1/rho), the rounded reciprocal of the moments, so no
+// kernel divides here), s = 2 u_x + a_x, A = fx s and B = fx u_y, and using
+// (c.u_s)^2 - (c.u)^2 = (c.a)(c.(2u + a)), |u_s|^2 - |u|^2 = a.(2u + a),
+// rho a = F and c_x^2 = 1:
+//   c_x = 0:    f_ext_i = -1.5 w_i A
+//   c_x = +-1:  f_ext_i = w_i (3 c_x fx + 3 A + 9 c_x c_y B)
 template <class T>
 __device__ __forceinline__ void add_edm_force_x(const MomentsT<T> &m, T fx, T out[Q]) {
   const T ax = v_mul(fx, m.inv_rho);
-  const T sx = v_fma(v_c<T>(2.0f), m.ux, ax);
-  const T uy2 = v_mul(v_c<T>(2.0f), m.uy);
-  const T m15s = v_mul(v_c<T>(-1.5f), sx);
+  const T A = v_mul(fx, v_fma(v_c<T>(2.0f), m.ux, ax));
+  const T B = v_mul(fx, m.uy);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const T wfx = v_mul(v_c<T>(wf(i)), fx);
+    const float w = wf(i);
     if (cx(i) == 0) {
-      out[i] = v_fma(wfx, m15s, out[i]);  // only the -1.5 a.(2u+a) term survives
+      out[i] = v_fma(v_c<T>(-1.5f * w), A, out[i]);
     } else {
-      const T csx = cx(i) > 0 ? sx : v_mul(v_c<T>(-1.0f), sx);
-      const T cs = cy(i) == 0 ? csx : (cy(i) > 0 ? v_add(csx, uy2) : v_sub(csx, uy2));
-      const T t = v_fma(cs, v_c<T>(4.5f), v_c<T>(3.0f));
-      out[i] = v_fma(wfx, v_fma(t, v_c<T>((float)cx(i)), m15s), out[i]);
+      // w (3 c_x fx) + w 3 A [+ w 9 c_x c_y B]
+      T t = v_fma(v_c<T>(3.0f * w * (float)cx(i)), fx, out[i]);
+      if (cy(i) != 0) t = v_fma(v_c<T>(9.0f * w * (float)(cx(i) * cy(i))), B, t);
+      out[i] = v_fma(v_c<T>(3.0f * w), A, t);
     }
   }
 }
