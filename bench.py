@@ -57,8 +57,89 @@ def _peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+class NvmlSampler:
+    """Clock, throttle-reason and power sampling through NVML (read-only queries,
+    ctypes) from a host thread every ~1 ms, so that a timed region of a few
+    milliseconds still has samples inside it.  `mark(t0, t1)` records the host
+    times of the timed region; only samples inside it are summarised."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_id=None, index=0):
+        import ctypes as C
+        import threading
+        self.C = C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.h = C.c_void_p()
+        # by UUID when known (NVML numbers the physical GPUs, whatever
+        # CUDA_VISIBLE_DEVICES says), else by index
+        rc = lib.nvmlDeviceGetHandleByUUID(C.c_char_p(gpu_id.encode()), C.byref(self.h)) \
+            if gpu_id else lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h))
+        if rc != 0:
+            raise RuntimeError("no NVML handle")
+        self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.rows, self.window = [], None
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _query(self):
+        C, lib = self.C, self.lib
+        clk, mx, pw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(clk))      # NVML_CLOCK_SM
+        lib.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(mx))
+        lib.nvmlDeviceGetPowerUsage(self.h, C.byref(pw))         # mW
+        self.reason_fn(self.h, C.byref(rs))
+        return clk.value, mx.value, pw.value / 1000.0, rs.value
+
+    def _run(self):
+        while not self.stop.is_set():
+            self.rows.append((time.perf_counter(), *self._query()))
+            time.sleep(0.001)
+
+    def __enter__(self):
+        self.thread.start()
+        time.sleep(0.05)
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.thread.join(timeout=5)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def summary(self):
+        rows = self.rows
+        if self.window:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            rows = inside or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        reasons = sorted({name for r in rows for bit, name in self.REASONS.items() if r[4] & bit})
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[3] for r in rows),
+                "source": "nvml, ~1 ms, samples inside the timed region"}
+
+
+def clock_sampler(gpu_id, index):
+    """NVML sampling if the library loads, else nvidia-smi."""
+    try:
+        return NvmlSampler(gpu_id, index)
+    except Exception:
+        return ClockSampler(gpu_id)
+
+
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region (fallback)."""
+
+    def mark(self, t0, t1):
+        pass
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -205,8 +286,10 @@ def run_gpu(args):
         str(uuid) if uuid is not None else None)
     _barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(gpu_id) as clk:
+    with clock_sampler(gpu_id, local) as clk:
+        t_host0 = time.perf_counter()
         ms, seg = _time_steps_segments(lat, "mlp_bf16", w, args.steps, torch, stream)
+        clk.mark(t_host0, time.perf_counter())
     torch.cuda.synchronize()
     _barrier(world)
     ms_max = _max_over_ranks(ms, world, dev)

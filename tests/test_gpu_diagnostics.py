@@ -102,3 +102,22 @@ def test_les_run_records_statistics(lbm):
     assert np.all(res["S"][:, 1, :] > 0) and np.all(np.diff(res["S"][-1, 1, :4]) > 0)
     xi = les.ess_exponents(res["S"].mean(0))
     assert abs(xi[2] - 1.0) < 1e-12 and np.all(np.isfinite(xi))
+
+
+def test_long_comparison_reports_the_unstable_step(lbm):
+    """The long-run comparison stops a run at the first status check (every
+    check_every steps) that finds |u| >= 0.4 or a non-finite value and reports
+    that step; statistics are kept only for the records before it.  A learned
+    collision with an oversized output layer blows up; Smagorinsky at tau 0.6
+    does not."""
+    from paper_2403_18466_gb300 import inputs, les
+    theta = torch.tensor(inputs.xavier_mlp(3, out_scale=3.0), dtype=torch.float32, device=DEV)
+    rec = les.long_comparison(theta, n=64, steps=600, every=200, tau=0.6, rmax=8,
+                              device=DEV, check_every=50)
+    ml, sm = rec["mlp_bf16"], rec["smag"]
+    assert ml["unstable_at"] is not None and ml["unstable_at"] % 50 == 0
+    assert ml["unstable_at"] <= 600
+    assert all(s < ml["unstable_at"] for s in ml["steps"])
+    assert len(ml["steps"]) == (ml["unstable_at"] - 1) // 200
+    assert sm["unstable_at"] is None and sm["steps"] == [200, 400, 600]
+    assert np.all(np.isfinite(sm["energy"])) and sm["ess"] is not None
