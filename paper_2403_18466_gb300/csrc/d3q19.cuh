@@ -8,6 +8,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "approx.cuh"
+
 namespace lbm {
 namespace d3 {
 
@@ -47,6 +49,7 @@ constexpr float UNSTABLE_USQ = 0.16f;  // |u| >= 0.4 marks the run unstable
 
 struct Moments {
   float drho, rho, ux, uy, uz;
+  float inv_rho;  // 1/rho
 };
 
 __device__ __forceinline__ Moments node_moments(const float d[Q]) {
@@ -62,6 +65,7 @@ __device__ __forceinline__ Moments node_moments(const float d[Q]) {
   m.drho = s;
   m.rho = 1.0f + s;
   const float inv = 1.0f / m.rho;
+  m.inv_rho = inv;
   m.ux = jx * inv;
   m.uy = jy * inv;
   m.uz = jz * inv;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void add_edm_force(const Moments &m, float Fx, float 
 
 // Smagorinsky tau_eff = (tau0 + sqrt(tau0^2 + 18 (C_s Delta)^2 Q / rho)) / 2 with
 // Q = sqrt(2 Pi:Pi), Pi_ab = sum c_ia c_ib (f_i - feq_i) (SI section 1).
-__device__ __forceinline__ float smag_omega(const float d[Q], const float deq[Q], float rho,
+__device__ __forceinline__ float smag_omega(const float d[Q], const float deq[Q], float inv_rho,
                                             float tau0_sq, float tau0, float c18) {
   float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
@@ -114,9 +118,7 @@ __device__ __forceinline__ float smag_omega(const float d[Q], const float deq[Q]
     if (cy(i) && cz(i)) pyz += cy(i) * cz(i) > 0 ? n : -n;
   }
   const float pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
-  const float Qs = sqrtf(2.0f * pp);
-  const float tau_eff = 0.5f * (tau0 + sqrtf(tau0_sq + c18 * Qs / rho));
-  return 1.0f / tau_eff;
+  return smagorinsky_omega(pp, inv_rho, tau0, tau0_sq, c18);
 }
 
 __device__ __forceinline__ bool is_unstable(const Moments &m) {

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(NT) k3_step(const float *__restrict__ in, floa
   pull(in, g, p, d);
   const Moments m = node_moments(d);
   shifted_feq(m, deq);
-  const float om = KIND == KIND_SMAG ? smag_omega(d, deq, m.rho, c.tau0_sq, c.tau, c.smag_c18)
+  const float om = KIND == KIND_SMAG ? smag_omega(d, deq, m.inv_rho, c.tau0_sq, c.tau, c.smag_c18)
                                      : c.omega;
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] += om * (deq[i] - d[i]);

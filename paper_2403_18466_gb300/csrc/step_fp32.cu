@@ -15,6 +15,7 @@
 // from the adjacent lane by a warp shuffle, and only the warp's edge lanes
 // (and the periodic wrap) issue an extra scalar load.  Stores are aligned
 // 128-bit.  Other widths take a one-node-per-thread kernel.
+#include "approx.cuh"
 #include "kernels.h"
 #include "lattice.cuh"
 
@@ -44,9 +45,8 @@ __device__ __forceinline__ bool collide_node(float d[Q], const CollideParams &p,
     const float pxx = (n[1] + n[3]) + ((n[5] + n[6]) + (n[7] + n[8]));
     const float pyy = (n[2] + n[4]) + ((n[5] + n[6]) + (n[7] + n[8]));
     const float pxy = (n[5] - n[6]) + (n[7] - n[8]);
-    const float qn = sqrtf(2.0f * (pxx * pxx + 2.0f * pxy * pxy + pyy * pyy));
-    const float tau_eff = 0.5f * (p.tau + sqrtf(p.tau0_sq + p.smag_c18 * qn / m.rho));
-    omega = 1.0f / tau_eff;
+    omega = smagorinsky_omega(pxx * pxx + 2.0f * pxy * pxy + pyy * pyy, m.inv_rho, p.tau,
+                              p.tau0_sq, p.smag_c18);
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] = bgk_relax(d[i], deq[i], omega);
