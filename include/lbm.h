@@ -146,6 +146,16 @@ int lbm_clear_status(lbm_ctx *ctx);
  * in flight.  Host-side only; LBM_ERR_ARG for a NULL context. */
 int lbm_set_wait_limit(lbm_ctx *ctx, unsigned polls);
 
+/* Launch shape of the tensor-core step (no counterpart in the paper): caps
+ * the persistent grid of LBM_MLP_BF16 steps at n CTAs for the later lbm_step
+ * calls of this context (0, the default, restores one CTA per SM).  With
+ * fewer CTAs each warpgroup walks more tiles, so a lattice small enough for
+ * an element-by-element check against a reference still exercises the
+ * kernel's tile-to-tile path (staging the next tile, crossing row and
+ * lattice boundaries) that large lattices take.  Results do not depend on
+ * n.  Host-side only; LBM_ERR_ARG for a NULL context or n < 0. */
+int lbm_set_max_ctas(lbm_ctx *ctx, int n);
+
 /* The hidden-layer activation of LBM_MLP_BF16 (tanh, Eq. S10 network) applied
  * element-wise, for checking its accuracy: out[k] = act(a[k]) for n FP32
  * pre-activations a (device arrays, caller-owned, asynchronous on

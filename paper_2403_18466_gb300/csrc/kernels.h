@@ -73,11 +73,12 @@ cudaError_t launch_step_mlp_f32(const Grid &g, const float *in, float *out,
 // mlp_bf16.cu ------------------------------------------------------------------
 // weights: FP32 (dtype 0) or BF16 (dtype 1), same packed row-major layout.
 // wait_limit: polls of each bounded mbarrier wait before the kernel gives up
-// and sets *timeout_flag (0 = the default, 2^20).
+// and sets *timeout_flag (0 = the default, 2^20); max_ctas: cap on the
+// persistent grid (0 = one CTA per SM).
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wptr[6], int dtype,
                                  int *flag, int *timeout_flag, cudaStream_t s,
-                                 unsigned wait_limit = 0);
+                                 unsigned wait_limit = 0, int max_ctas = 0);
 
 // Compiled layout of the tensor-core step: tile warpgroups per SM and, of
 // every 8 activation pairs, how many the XU evaluates.

@@ -124,22 +124,24 @@ __device__ __forceinline__ T bgk_relax(T d, T deq, T omega) {
 // (c.u_s)^2 - (c.u)^2 = (c.a)(c.(2u + a)), |u_s|^2 - |u|^2 = a.(2u + a),
 // rho a = F and c_x^2 = 1:
 //   c_x = 0:    f_ext_i = -1.5 w_i A
-//   c_x = +-1:  f_ext_i = w_i (3 c_x fx + 3 A + 9 c_x c_y B)
+//   c_x = +-1:  f_ext_i = 3 w_i (E_cx + 3 c_x c_y B),  E_+ = A + fx, E_- = A - fx
+// (one or two fused multiply-adds per population).  Called with fx = 0 on a
+// lattice without forcing, where it adds zeros.
 template <class T>
 __device__ __forceinline__ void add_edm_force_x(const MomentsT<T> &m, T fx, T out[Q]) {
   const T ax = v_mul(fx, m.inv_rho);
   const T A = v_mul(fx, v_fma(v_c<T>(2.0f), m.ux, ax));
   const T B = v_mul(fx, m.uy);
+  const T Ep = v_add(A, fx), Em = v_sub(A, fx);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const float w = wf(i);
     if (cx(i) == 0) {
       out[i] = v_fma(v_c<T>(-1.5f * w), A, out[i]);
     } else {
-      // w (3 c_x fx) + w 3 A [+ w 9 c_x c_y B]
-      T t = v_fma(v_c<T>(3.0f * w * (float)cx(i)), fx, out[i]);
-      if (cy(i) != 0) t = v_fma(v_c<T>(9.0f * w * (float)(cx(i) * cy(i))), B, t);
-      out[i] = v_fma(v_c<T>(3.0f * w), A, t);
+      T e = cx(i) > 0 ? Ep : Em;
+      if (cy(i) != 0) e = v_fma(v_c<T>(3.0f * (float)(cx(i) * cy(i))), B, e);
+      out[i] = v_fma(v_c<T>(3.0f * w), e, out[i]);
     }
   }
 }

@@ -37,6 +37,7 @@ struct lbm_ctx {
   size_t diag_part_cap;
   void *fft_plan;
   unsigned wait_limit;  // polls per bounded device wait of the tensor-core kernels (0: default)
+  int max_ctas;         // CTAs of the tensor-core step (0: one per SM)
   // last lbm_forward_record
   int rec_n, rec_k;
   const void *rec_ws;
@@ -98,7 +99,7 @@ cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind
     case LBM_MLP_BF16: {
       const void *wp[6] = {w->w1, w->b1, w->w2, w->b2, w->w3, w->b3};
       return lbm::launch_step_mlp_bf16(c->g, in, out, c->cp, wp, w->dtype, c->d_flag,
-                                       c->d_flag + 1, c->stream, c->wait_limit);
+                                       c->d_flag + 1, c->stream, c->wait_limit, c->max_ctas);
     }
   }
   return cudaErrorInvalidValue;
@@ -290,6 +291,12 @@ int lbm_activation(const float *a, int n, int path, float *out, void *cuda_strea
 int lbm_set_wait_limit(lbm_ctx *c, unsigned polls) {
   if (!c) return LBM_ERR_ARG;
   c->wait_limit = polls;
+  return LBM_OK;
+}
+
+int lbm_set_max_ctas(lbm_ctx *c, int n) {
+  if (!c || n < 0) return LBM_ERR_ARG;
+  c->max_ctas = n;
   return LBM_OK;
 }
 

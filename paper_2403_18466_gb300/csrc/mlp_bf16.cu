@@ -264,14 +264,14 @@ __device__ __forceinline__ void pull_node(const float *__restrict__ in, size_t p
 // x = (f - feq)/rho written as row r of the layer-1 operand (9 inputs, the
 // constant-1 bias column, zeros; bf16 with integer rounding on the ALU), the
 // BGK + force update (the same helpers as the BGK kernel, so a zero output
-// layer reproduces BGK bit for bit) and rho/tau.  Returns true for an
-// unstable node.
+// layer reproduces BGK bit for bit; fx = 0 on a lattice without forcing, so
+// there is no branch) and rho/tau.  Returns true for an unstable node.
 struct NodePrep {
   float base[Q];
   float rw;
 };
-__device__ __forceinline__ bool prep_node(const float d[Q], float omega, const float *force,
-                                          float fx, unsigned char *a1, int r, NodePrep &P) {
+__device__ __forceinline__ bool prep_node(const float d[Q], float omega, float fx,
+                                          unsigned char *a1, int r, NodePrep &P) {
   const Moments m = node_moments(d);
   float deq[Q];
   shifted_feq(m, deq);
@@ -285,7 +285,7 @@ __device__ __forceinline__ bool prep_node(const float d[Q], float omega, const f
       make_uint4(pack_bf16x2_alu(xin[8], 1.0f), 0u, 0u, 0u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) P.base[i] = bgk_relax(d[i], deq[i], omega);
-  if (force) add_edm_force_x(m, fx, P.base);
+  add_edm_force_x(m, fx, P.base);
   P.rw = m.rho * omega;
   return is_unstable(m);
 }
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int i = 0; i < Q; ++i) d[i] = 0.f;
     const bool act = count > 0 && T.x0 + r < nx;
     if (act) pull_node(in, plane, nx, ny, T, T.x0 + r, d);
-    const bool b0 = prep_node(d, omega, p.force,
-                              (count > 0 && p.force) ? __ldg(p.force + T.y) : 0.f, a1, r, P);
+    const bool b0 =
+        prep_node(d, omega, (count > 0 && p.force) ? __ldg(p.force + T.y) : 0.f, a1, r, P);
     bad = act && b0;
   }
 
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // tile has read a1)
     NodePrep Pn;
     {
-      const bool bn = prep_node(dn, omega, p.force, fxn, a1, r, Pn);
+      const bool bn = prep_node(dn, omega, fxn, a1, r, Pn);
       bad |= nact && bn;
     }
 
@@ -560,7 +560,7 @@ cudaError_t launch_activation(const float *a, int n, int path, float *out, cudaS
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wp[6], int dtype,
                                  int *flag, int *timeout_flag, cudaStream_t s,
-                                 unsigned wait_limit) {
+                                 unsigned wait_limit, int max_ctas) {
   static int sms = 0;
   static bool attr_done[2] = {false, false};
   if (!sms) {
@@ -579,6 +579,7 @@ cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
   const long long tiles = (long long)((g.nx + WG_THREADS - 1) / WG_THREADS) * g.ny * g.batch;
   long long ctas = (tiles + WGS - 1) / WGS;
   if (ctas > (long long)sms) ctas = sms;
+  if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
   if (wait_limit == 0) wait_limit = DEFAULT_WAIT_LIMIT;
   kern<<<(unsigned)ctas, THREADS, SMEM_BYTES, s>>>(in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1],
                                                    wp[2], wp[3], wp[4], wp[5], flag, timeout_flag,

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(THREADS)
     const float rw = m.rho * p.omega;  // rho / tau
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = fmaf(p.omega, deq[i] - d[i], d[i]) + rw * o[i];
-    if (p.force) add_edm_force_x(m, __ldg(p.force + y), d);
+    add_edm_force_x(m, p.force ? __ldg(p.force + y) : 0.0f, d);
 #pragma unroll
     for (int i = 0; i < Q; ++i) ob[i * plane + (size_t)y * nx + x] = d[i];
   }

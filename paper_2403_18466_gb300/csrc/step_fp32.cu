@@ -50,7 +50,7 @@ __device__ __forceinline__ bool collide_node(float d[Q], const CollideParams &p,
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] = bgk_relax(d[i], deq[i], omega);
-  if (p.force) add_edm_force_x(m, fx, d);
+  add_edm_force_x(m, fx, d);  // fx = 0 without forcing
   return bad;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "lbm_status": (_i, [_vp]),
     "lbm_clear_status": (_i, [_vp]),
     "lbm_set_wait_limit": (_i, [_vp, C.c_uint]),
+    "lbm_set_max_ctas": (_i, [_vp, _i]),
     "lbm_activation": (_i, [_vp, _i, _i, _vp, _vp]),
     "lbm_mlp_bf16_layout": (_i, [C.POINTER(_i), C.POINTER(_i)]),
     "lbm_velocity_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -292,6 +293,10 @@ class Lattice:
     def set_wait_limit(self, polls):
         """Polls per bounded device wait of the tensor-core step (0 = default)."""
         _check(self.lib.lbm_set_wait_limit(self.ctx, int(polls)), "lbm_set_wait_limit")
+
+    def set_max_ctas(self, n):
+        """Cap on the tensor-core step's persistent grid (0 = one CTA per SM)."""
+        _check(self.lib.lbm_set_max_ctas(self.ctx, int(n)), "lbm_set_max_ctas")
 
     # -- training -----------------------------------------------------------
     def velocity_loss(self, utx, uty, want_grad=True):

@@ -91,6 +91,7 @@ def test_mlp_bf16_layout_query(lib):
 def test_host_side_argument_errors_of_the_test_hooks(lib):
     from paper_2403_18466_gb300 import lbm
     assert lib.lbm_set_wait_limit(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_set_max_ctas(None, 1) == lbm.LBM_ERR_ARG
     assert lib.lbm_activation(None, 4, 0, None, None) == lbm.LBM_ERR_ARG
     fake = C.c_void_p(256)
     assert lib.lbm_activation(fake, 4, 3, fake, None) == lbm.LBM_ERR_ARG

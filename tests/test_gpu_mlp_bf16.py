@@ -58,16 +58,36 @@ def _bench_theta():
     return inputs.xavier_mlp(3, out_scale=0.3)
 
 
-SHAPES = [(256, 64, 1), (130, 33, 2), (64, 64, 1), (37, 5, 1), (1, 1, 1), (4096, 3, 1)]
+# nx % 4 == 0 takes the kernel's bulk-copy staging of the populations: full
+# tiles, a single partial tile, a partial last tile (200, 132), the smallest
+# width (4), one row (ny = 1: both y-neighbours are the row itself) and
+# batches; other widths load each node's populations directly.
+SHAPES = [(256, 64, 1), (130, 33, 2), (64, 64, 1), (37, 5, 1), (1, 1, 1), (4096, 3, 1),
+          (200, 7, 2), (4, 3, 1), (132, 1, 3)]
 
 
 @pytest.mark.parametrize("nx,ny,B", SHAPES)
 def test_one_step_population_and_velocity_parity(lbm, nx, ny, B, record_property):
+    _two_step_parity(lbm, nx, ny, B, record_property)
+
+
+# One CTA (eight warpgroups) or three for the whole lattice: every warpgroup
+# walks many tiles, across rows and lattices of the batch, with the next
+# tile's populations staged while the current one runs (nx % 4 == 0) or
+# loaded directly (other widths), as on large lattices.
+@pytest.mark.parametrize("nx,ny,B,ctas", [(256, 40, 2, 1), (200, 23, 1, 3), (132, 9, 3, 1),
+                                          (130, 17, 2, 1), (4, 50, 2, 1)])
+def test_tile_walk_parity(lbm, nx, ny, B, ctas, record_property):
+    _two_step_parity(lbm, nx, ny, B, record_property, ctas=ctas)
+
+
+def _two_step_parity(lbm, nx, ny, B, record_property, ctas=0):
     tau, F0, m = 0.6, 1e-4, 1
     theta = _theta()
     thb = bf16_round(theta)
     f = population_field(B, ny, nx, seed=nx + 3 * ny)
     lat = lbm.Lattice(nx, ny, B, tau=tau, force_amp=F0, force_mode=m, device=DEV)
+    lat.set_max_ctas(ctas)
     w = lbm.weights_struct(_dev(theta))
     lat.set_state(_dev(f))
     g = oracle.stream_push(f.astype(np.float64))
@@ -86,9 +106,10 @@ def test_one_step_population_and_velocity_parity(lbm, nx, ny, B, record_property
         _, sx, sy = oracle.moments(oracle.stream_pull(ref64))
         eu, eu64, du = rel_vel_err(gx, gy, rx, ry), rel_vel_err(gx, gy, sx, sy), \
             rel_vel_err(bx, by, rx, ry)
-        msg = (f"{nx}x{ny}x{B} step {step}: pop err {err:.3e} (tol {tol:.3e}, correction "
-               f"{corr:.3e}, err/corr {err / corr:.3e}), err64 {err64:.3e}; velocity err "
-               f"{eu:.3e}, err64 {eu64:.3e}, BGK-vs-learned {du:.3e}")
+        msg = (f"{nx}x{ny}x{B} ctas {ctas or 'all'} step {step}: pop err {err:.3e} "
+               f"(tol {tol:.3e}, correction {corr:.3e}, err/corr {err / corr:.3e}), "
+               f"err64 {err64:.3e}; velocity err {eu:.3e}, err64 {eu64:.3e}, "
+               f"BGK-vs-learned {du:.3e}")
         print(msg)
         record_property(f"step{step}", msg)
         assert corr > 10 * tol and corr > 1e-2, msg  # the guard: BGK is far outside
