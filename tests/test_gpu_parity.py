@@ -212,3 +212,29 @@ def test_argument_errors(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lat.box_filter(3)
     assert e.value.code == lbm.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("nx,ny", [(256, 6), (130, 5)])
+@pytest.mark.parametrize("kind", ["bgk", "smag", "mlp_f32", "mlp_bf16"])
+def test_uniform_equilibrium_is_a_fixed_point(lbm, kind, nx, ny):
+    """A uniform equilibrium (constant rho and u, no forcing) stays in place
+    under every collision: streaming moves equal values onto each other, BGK
+    and Smagorinsky relax f = feq onto itself (Pi^neq = 0, so tau_eff = tau;
+    Eq. S3 and SI section 1), and a network without biases maps
+    x = (f - feq)/rho = 0 to o = 0 (Eq. S10).  With biases the learned kinds
+    move it, so the check on them is not vacuous.  Tolerance: FP32 rounding of
+    the recomputed moments and equilibrium over 10 steps."""
+    B = 2
+    shape = (B, ny, nx)
+    lat = lbm.Lattice(nx, ny, B, tau=0.55, smag_cs=0.1, device=DEV)
+    lat.init_equilibrium(_dev(np.full(shape, 1.02)), _dev(np.full(shape, 0.03)),
+                         _dev(np.full(shape, -0.02)))
+    f0 = _np(lat.get_state())
+    theta = inputs.xavier_mlp(4, out_scale=0.3)  # no biases
+    lat.step(10, kind, lbm.weights_struct(_dev(theta)))
+    assert rel_pop_err(_np(lat.get_state()), f0) <= 1e-6
+    if kind.startswith("mlp"):
+        biased = inputs.xavier_mlp(4, bias_scale=0.3, out_scale=0.3)
+        lat.set_state(_dev(f0))
+        lat.step(1, kind, lbm.weights_struct(_dev(biased)))
+        assert rel_pop_err(_np(lat.get_state()), f0) > 1e-3
