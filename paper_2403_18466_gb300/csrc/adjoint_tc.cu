@@ -8,10 +8,16 @@
 //   lam_i(x - c_i) = [J_C(f(x))^T lam'(x)]_i,   dtheta += sum_x (dC/dtheta)^T lam'(x).
 //
 // A warpgroup owns a 128-node tile (thread r = node r = TMEM lane r) and runs
-// six GEMMs with M = 128 nodes:
-//   forward recompute   x|1 . W1'^T -> tanh -> h1|1 . W2'^T -> tanh -> h2|1 . W3'^T = o
+// five GEMMs with M = 128 nodes:
+//   forward recompute   x|1 . W1'^T -> tanh -> h1|1 . W2'^T -> tanh -> h2
 //   backward            dL/do . W3 -> *(1-h2^2) = dL/da2 ;  dL/da2 . W2 -> *(1-h1^2) = dL/da1 ;
 //                       dL/da1 . W1 = dL/dx
+// The network output o is not recomputed: the update f' = ... + (rho/tau) P o
+// needs it only in the rho-derivative of its scaling, sum_i (dL/df'_i omega)
+// (P o)_i = (dL/do . o) / rho with dL/do = rho omega P dL/df' (P symmetric),
+// and dL/do . o = (W3^T dL/do) . h2 + dL/do . b3, where W3^T dL/do is the first
+// backward GEMM's result: a dot product in that GEMM's epilogue instead of a
+// GEMM round trip.
 // The weight gradients are three GEMMs with the NODES as the reduction
 // dimension (K = 16 nodes per MMA), M = 64 hidden units, reading the same
 // node-row operand buffers as MN-major matrices:
@@ -70,7 +76,6 @@ struct __align__(16) WgBuffers {
 struct __align__(1024) Smem {
   unsigned char w1[HIDDEN * K1 * 2];  // [64 x 16]  W1 | b1
   unsigned char w2[HIDDEN * K2 * 2];  // [64 x 80]  W2 | b2
-  unsigned char w3[16 * K2 * 2];      // [16 x 80]  W3 | b3
   unsigned char w3t[HIDDEN * 16 * 2]; // [64 x 16]  [j][i] = W3[i][j]
   unsigned char w2t[HIDDEN * 64 * 2]; // [64 x 64]  [k][j] = W2[j][k]
   unsigned char w1t[16 * 64 * 2];     // [16 x 64]  [i][j] = W1[j][i]
@@ -80,6 +85,7 @@ struct __align__(1024) Smem {
   unsigned long long dwd[WGS][STAGES];  // that GEMM has completed (commit)
   unsigned long long drain[STAGES];
   float db3[WGS * 4][9];
+  float b3[16];                       // b3 rounded to bf16, as floats
   uint32_t taddr;
   int err;
 };
@@ -225,6 +231,39 @@ __device__ __forceinline__ void dtanh_row(uint32_t tm_row, uint32_t tm_dh, unsig
   }
 }
 
+// As dtanh_row, and also returns sum_k D_k h_k over the 64 columns, with h
+// the bf16 row r of `h` (row length K2).
+__device__ __forceinline__ float dtanh_row_dot(uint32_t tm_row, uint32_t tm_dh,
+                                               unsigned char *dst, const unsigned char *h,
+                                               int r) {
+  float dot0 = 0.f, dot1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < HIDDEN; c += 32) {
+    uint32_t v[32], dh[16];
+    tmem_ld32(tm_row + c, v);
+    tmem_ld16(tm_dh + c / 2, dh);
+    tmem_wait_ld();
+    uint32_t p[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+      p[e] = pack_bf16x2(__uint_as_float(v[2 * e]) * bf16_lo(dh[e]),
+                         __uint_as_float(v[2 * e + 1]) * bf16_hi(dh[e]));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      *reinterpret_cast<uint4 *>(dst + canon_offset(r, c + 8 * e, 64)) =
+          make_uint4(p[4 * e], p[4 * e + 1], p[4 * e + 2], p[4 * e + 3]);
+      const uint4 hv = *reinterpret_cast<const uint4 *>(h + canon_offset(r, c + 8 * e, K2));
+      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dot0 = fmaf(__uint_as_float(v[8 * e + 2 * q]), bf16_lo(hw[q]), dot0);
+        dot1 = fmaf(__uint_as_float(v[8 * e + 2 * q + 1]), bf16_hi(hw[q]), dot1);
+      }
+    }
+  }
+  return dot0 + dot1;
+}
+
 struct TilePos {
   int b, y, x0;
   __device__ __forceinline__ void advance(int nx, int ny) {
@@ -289,12 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n = e / K2, k = e % K2;
     store_bf16(S.w2, n, k, K2, k < HIDDEN ? w.w2[n * HIDDEN + k] : (k == HIDDEN ? w.b2[n] : 0.f));
   }
-  for (int e = tid; e < 16 * K2; e += THREADS) {
-    const int n = e / K2, k = e % K2;
-    float v = 0.f;
-    if (n < 9) v = k < HIDDEN ? w.w3[n * HIDDEN + k] : (k == HIDDEN ? w.b3[n] : 0.f);
-    store_bf16(S.w3, n, k, K2, v);
-  }
+  if (tid < 16) S.b3[tid] = tid < 9 ? __bfloat162float(__float2bfloat16_rn(w.b3[tid])) : 0.f;
   for (int e = tid; e < HIDDEN * 16; e += THREADS) {
     const int j = e / 16, i = e % 16;
     store_bf16(S.w3t, j, i, 16, i < 9 ? w.w3[i * HIDDEN + j] : 0.f);
@@ -421,7 +455,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t bar = smem_u32(&S.bar[wg]);
     const uint32_t s_a1 = smem_u32(B.a1), s_h1 = smem_u32(B.h1), s_h2 = smem_u32(B.h2);
     const uint32_t s_ob = smem_u32(B.ob), s_a2b = smem_u32(B.a2b);
-    const uint32_t s_w1 = smem_u32(S.w1), s_w2 = smem_u32(S.w2), s_w3 = smem_u32(S.w3);
+    const uint32_t s_w1 = smem_u32(S.w1), s_w2 = smem_u32(S.w2);
     const uint32_t s_w3t = smem_u32(S.w3t), s_w2t = smem_u32(S.w2t), s_w1t = smem_u32(S.w1t);
     constexpr uint32_t ID64 = idesc_bf16_f32(128, 64), ID16 = idesc_bf16_f32(128, 16);
     unsigned char *a1b = B.h2;  // dL/da1 takes the h2 buffer once dW3 has read it
@@ -542,33 +576,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       WAIT_OWN_OR_BREAK()
       tanh_row(tm_row, B.h2, r, tm_wg + C_DH2 + lane_off);
-      OPERANDS_READY()
-      if (leader) {
-        fence_after_sync();
-#pragma unroll
-        for (int s = 0; s < K2 / 16; ++s)
-          mma_bf16(tm_wg + C_D, smem_desc(s_h2 + 256 * s, 128, 16 * K2),
-                   smem_desc(s_w3 + 256 * s, 128, 16 * K2), ID16, s > 0);
-        mma_commit(bar);
-        pending = true;
-      }
-      WAIT_OWN_OR_BREAK()
-      // ---- output of the network, then the reverse pass down to dL/do (FP32)
+      // ---- the reverse pass down to dL/do (FP32); the output's own term of
+      // the rho-derivative, (dL/do . o)/rho, follows the first backward GEMM
       // post = d + omega (deq - d) + rho omega ohat + fext(rho, u)
-      float rhob = 0.f, uxb = 0.f, uyb = 0.f;
+      float rhob = 0.f, uxb = 0.f, uyb = 0.f, ob_b3 = 0.f;
       {
-        float oh[Q], ob[Q];
-        uint32_t ov[16];
-        tmem_ld16(tm_row, ov);
-        tmem_wait_ld();
+        float ob[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) oh[i] = __uint_as_float(ov[i]);
-        project9(oh);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          ob[i] = m.rho * omega * pb[i];
-          rhob = fmaf(omega * pb[i], oh[i], rhob);
-        }
+        for (int i = 0; i < Q; ++i) ob[i] = m.rho * omega * pb[i];
         if (p.force) {
           // f_ext = feq(rho, u + a) - feq(rho, u), a = (fx/rho, 0): the
           // differences of the two sums, written without cancellation
@@ -587,7 +602,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         project9(ob);  // dL/do = P dL/dohat (P symmetric)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) db3[i] += ob[i];
+        for (int i = 0; i < Q; ++i) {
+          db3[i] += ob[i];
+          ob_b3 = fmaf(ob[i], S.b3[i], ob_b3);
+        }
         *reinterpret_cast<uint4 *>(B.ob + canon_offset(r, 0, 16)) =
             make_uint4(pack_bf16x2(ob[0], ob[1]), pack_bf16x2(ob[2], ob[3]),
                        pack_bf16x2(ob[4], ob[5]), pack_bf16x2(ob[6], ob[7]));
@@ -604,7 +622,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         pending = true;
       }
       WAIT_OWN_OR_BREAK()
-      dtanh_row(tm_row, tm_wg + C_DH2 + lane_off, B.a2b, r);
+      rhob = fmaf(dtanh_row_dot(tm_row, tm_wg + C_DH2 + lane_off, B.a2b, B.h2, r) + ob_b3, inv_rho,
+                  rhob);
       OPERANDS_READY()
       if (leader) {
         mbar_arrive(smem_u32(&S.rdy[wg][ST_DW2]));  // dL/da2 and h1 complete
