@@ -8,16 +8,18 @@
 //   lam_i(x - c_i) = [J_C(f(x))^T lam'(x)]_i,   dtheta += sum_x (dC/dtheta)^T lam'(x).
 //
 // A warpgroup owns a 128-node tile (thread r = node r = TMEM lane r) and runs
-// five GEMMs with M = 128 nodes:
-//   forward recompute   x|1 . W1'^T -> tanh -> h1|1 . W2'^T -> tanh -> h2
-//   backward            dL/do . W3 -> *(1-h2^2) = dL/da2 ;  dL/da2 . W2 -> *(1-h1^2) = dL/da1 ;
-//                       dL/da1 . W1 = dL/dx
+// five GEMMs with M = 128 nodes in four round trips:
+//   1. x|1 . W1'^T (layer 1 recomputed) and dL/do . W3 = dL/dh2 (dL/do needs only
+//      the incoming adjoint and rho), issued together;
+//   2. h1|1 . W2'^T (layer 2), whose epilogue forms h2 = tanh and, with the
+//      parked dL/dh2, dL/da2 = dL/dh2 (1 - h2^2);
+//   3. dL/da2 . W2 -> *(1 - h1^2) = dL/da1;   4. dL/da1 . W1 = dL/dx.
 // The network output o is not recomputed: the update f' = ... + (rho/tau) P o
 // needs it only in the rho-derivative of its scaling, sum_i (dL/df'_i omega)
 // (P o)_i = (dL/do . o) / rho with dL/do = rho omega P dL/df' (P symmetric),
 // and dL/do . o = (W3^T dL/do) . h2 + dL/do . b3, where W3^T dL/do is the first
-// backward GEMM's result: a dot product in that GEMM's epilogue instead of a
-// GEMM round trip.
+// backward GEMM's result: a dot product in the layer-2 epilogue, where dL/dh2
+// meets h2, instead of a GEMM round trip.
 // The weight gradients are three GEMMs with the NODES as the reduction
 // dimension (K = 16 nodes per MMA), M = 64 hidden units, reading the same
 // node-row operand buffers as MN-major matrices:
@@ -25,8 +27,8 @@
 // (db3 = sum dL/do on the CUDA cores).
 //
 // Organisation (one persistent CTA per SM): three warpgroups, each with one
-// tile in flight and its own 128 tensor-memory columns (accumulator and the
-// two tanh derivatives), plus three issuer warps, one per weight-gradient
+// tile in flight and its own 128 tensor-memory columns (accumulator, dL/dh2
+// then the layer-1 tanh derivative), plus three issuer warps, one per weight-gradient
 // GEMM (dW3, dW2, dW1), each accumulating the whole CTA's sum of its matrix
 // (112 columns in all).  A warpgroup signals the issuer concerned as soon as
 // the operands of that GEMM are complete (dL/do, then dL/da2, then dL/da1) and
@@ -56,9 +58,10 @@ constexpr int DW_WARP = WGS * 4;        // warp index of the first weight-gradie
 constexpr int THREADS = WGS * WG_THREADS + 3 * 32;
 constexpr int K1 = 16, K2 = 80;
 constexpr uint32_t TMEM_COLS = 512;
-// per-warpgroup block: GEMM accumulator, tanh derivatives 1 - h^2 of both
-// hidden layers (bf16 pairs)
-constexpr uint32_t C_D = 0, C_DH1 = 64, C_DH2 = 96, WG_COLS = 128;
+// per-warpgroup block: GEMM accumulator (64 columns) and 64 columns that hold
+// the first backward GEMM's result dL/dh2 until layer 1's epilogue, then the
+// layer-1 tanh derivative 1 - h1^2 (bf16 pairs, 32 columns)
+constexpr uint32_t C_D = 0, C_DH1 = 64, WG_COLS = 128;
 // weight-gradient sums of the CTA (M = 64 accumulators)
 constexpr uint32_t C_DW2 = WGS * WG_COLS, C_DW1 = C_DW2 + 80, C_DW3 = C_DW1 + 16;
 static_assert(C_DW3 + 16 <= TMEM_COLS, "tensor memory layout");
@@ -231,34 +234,56 @@ __device__ __forceinline__ void dtanh_row(uint32_t tm_row, uint32_t tm_dh, unsig
   }
 }
 
-// As dtanh_row, and also returns sum_k D_k h_k over the 64 columns, with h
-// the bf16 row r of `h` (row length K2).
-__device__ __forceinline__ float dtanh_row_dot(uint32_t tm_row, uint32_t tm_dh,
-                                               unsigned char *dst, const unsigned char *h,
-                                               int r) {
+// The first backward GEMM's result dL/dh2 (64 accumulator columns at tm)
+// -> bf16 row r of `g` (row length 64), where the layer-2 epilogue reads it.
+__device__ __forceinline__ void park_row(uint32_t tm, unsigned char *g, int r) {
+#pragma unroll
+  for (int c = 0; c < HIDDEN; c += 32) {
+    uint32_t v[32];
+    tmem_ld32(tm + c, v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      *reinterpret_cast<uint4 *>(g + canon_offset(r, c + 8 * e, 64)) =
+          make_uint4(pack_bf16x2(__uint_as_float(v[8 * e]), __uint_as_float(v[8 * e + 1])),
+                     pack_bf16x2(__uint_as_float(v[8 * e + 2]), __uint_as_float(v[8 * e + 3])),
+                     pack_bf16x2(__uint_as_float(v[8 * e + 4]), __uint_as_float(v[8 * e + 5])),
+                     pack_bf16x2(__uint_as_float(v[8 * e + 6]), __uint_as_float(v[8 * e + 7])));
+  }
+}
+
+// Layer-2 epilogue with the reverse step fused: h2 = tanh(D) as the bf16 row
+// r of `hdst` (the dW3 operand), and with g = dL/dh2 from the bf16 row r of
+// `g`, dL/da2 = g (1 - h2^2) written back over g.  Returns sum_k g_k h2_k
+// (h2 as stored), the output's term of the rho-derivative before its 1/rho.
+__device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *hdst,
+                                               unsigned char *g, int r) {
   float dot0 = 0.f, dot1 = 0.f;
 #pragma unroll
   for (int c = 0; c < HIDDEN; c += 32) {
-    uint32_t v[32], dh[16];
+    uint32_t v[32];
     tmem_ld32(tm_row + c, v);
-    tmem_ld16(tm_dh + c / 2, dh);
     tmem_wait_ld();
-    uint32_t p[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e)
-      p[e] = pack_bf16x2(__uint_as_float(v[2 * e]) * bf16_lo(dh[e]),
-                         __uint_as_float(v[2 * e + 1]) * bf16_hi(dh[e]));
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      *reinterpret_cast<uint4 *>(dst + canon_offset(r, c + 8 * e, 64)) =
-          make_uint4(p[4 * e], p[4 * e + 1], p[4 * e + 2], p[4 * e + 3]);
-      const uint4 hv = *reinterpret_cast<const uint4 *>(h + canon_offset(r, c + 8 * e, K2));
-      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+      const uint4 gv = *reinterpret_cast<const uint4 *>(g + canon_offset(r, c + 8 * e, 64));
+      const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w};
+      uint32_t hp[4], ap[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        dot0 = fmaf(__uint_as_float(v[8 * e + 2 * q]), bf16_lo(hw[q]), dot0);
-        dot1 = fmaf(__uint_as_float(v[8 * e + 2 * q + 1]), bf16_hi(hw[q]), dot1);
+        float h0, h1, d0, d1;
+        tanh_and_slope(__uint_as_float(v[8 * e + 2 * q]), h0, d0);
+        tanh_and_slope(__uint_as_float(v[8 * e + 2 * q + 1]), h1, d1);
+        hp[q] = pack_bf16x2(h0, h1);
+        const float g0 = bf16_lo(gw[q]), g1 = bf16_hi(gw[q]);
+        ap[q] = pack_bf16x2(g0 * d0, g1 * d1);
+        dot0 = fmaf(g0, bf16_lo(hp[q]), dot0);
+        dot1 = fmaf(g1, bf16_hi(hp[q]), dot1);
       }
+      *reinterpret_cast<uint4 *>(hdst + canon_offset(r, c + 8 * e, K2)) =
+          make_uint4(hp[0], hp[1], hp[2], hp[3]);
+      *reinterpret_cast<uint4 *>(g + canon_offset(r, c + 8 * e, 64)) =
+          make_uint4(ap[0], ap[1], ap[2], ap[3]);
     }
   }
   return dot0 + dot1;
@@ -554,30 +579,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 8, K1)) =
             make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
       }
-      OPERANDS_READY()
-      if (leader) {
-        fence_after_sync();
-        mma_bf16(tm_wg + C_D, smem_desc(s_a1, 128, 16 * K1), smem_desc(s_w1, 128, 16 * K1), ID64,
-                 0);
-        mma_commit(bar);
-        pending = true;
-      }
-      WAIT_OWN_OR_BREAK()
-      tanh_row(tm_row, B.h1, r, tm_wg + C_DH1 + lane_off);
-      OPERANDS_READY()
-      if (leader) {
-        fence_after_sync();
-#pragma unroll
-        for (int s = 0; s < K2 / 16; ++s)
-          mma_bf16(tm_wg + C_D, smem_desc(s_h1 + 256 * s, 128, 16 * K2),
-                   smem_desc(s_w2 + 256 * s, 128, 16 * K2), ID64, s > 0);
-        mma_commit(bar);
-        pending = true;
-      }
-      WAIT_OWN_OR_BREAK()
-      tanh_row(tm_row, B.h2, r, tm_wg + C_DH2 + lane_off);
-      // ---- the reverse pass down to dL/do (FP32); the output's own term of
-      // the rho-derivative, (dL/do . o)/rho, follows the first backward GEMM
+      // ---- dL/do (FP32) needs only the incoming adjoint and rho, so its GEMM
+      // (dL/dh2 = dL/do . W3) runs beside layer 1
       // post = d + omega (deq - d) + rho omega ohat + fext(rho, u)
       float rhob = 0.f, uxb = 0.f, uyb = 0.f, ob_b3 = 0.f;
       {
@@ -614,18 +617,32 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       OPERANDS_READY()
       if (leader) {
-        mbar_arrive(smem_u32(&S.rdy[wg][ST_DW3]));  // h2 and dL/do complete
         fence_after_sync();
-        // dL/da2 (before the tanh derivative) = dL/do . W3
-        mma_bf16(tm_wg + C_D, smem_desc(s_ob, 128, 256), smem_desc(s_w3t, 128, 256), ID64, 0);
+        mma_bf16(tm_wg + C_D, smem_desc(s_a1, 128, 16 * K1), smem_desc(s_w1, 128, 16 * K1), ID64,
+                 0);
+        // into the derivative columns, free until layer 1's epilogue
+        mma_bf16(tm_wg + C_DH1, smem_desc(s_ob, 128, 256), smem_desc(s_w3t, 128, 256), ID64, 0);
         mma_commit(bar);
         pending = true;
       }
       WAIT_OWN_OR_BREAK()
-      rhob = fmaf(dtanh_row_dot(tm_row, tm_wg + C_DH2 + lane_off, B.a2b, B.h2, r) + ob_b3, inv_rho,
-                  rhob);
+      park_row(tm_wg + C_DH1 + lane_off, B.a2b, r);  // read before the derivative overwrites it
+      tanh_row(tm_row, B.h1, r, tm_wg + C_DH1 + lane_off);
       OPERANDS_READY()
       if (leader) {
+        fence_after_sync();
+#pragma unroll
+        for (int s = 0; s < K2 / 16; ++s)
+          mma_bf16(tm_wg + C_D, smem_desc(s_h1 + 256 * s, 128, 16 * K2),
+                   smem_desc(s_w2 + 256 * s, 128, 16 * K2), ID64, s > 0);
+        mma_commit(bar);
+        pending = true;
+      }
+      WAIT_OWN_OR_BREAK()
+      rhob = fmaf(tanh_grad_row(tm_row, B.h2, B.a2b, r) + ob_b3, inv_rho, rhob);
+      OPERANDS_READY()
+      if (leader) {
+        mbar_arrive(smem_u32(&S.rdy[wg][ST_DW3]));  // h2 and dL/do complete
         mbar_arrive(smem_u32(&S.rdy[wg][ST_DW2]));  // dL/da2 and h1 complete
         fence_after_sync();
         // dL/da1 (before the tanh derivative) = dL/da2 . W2
