@@ -396,6 +396,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = S.taddr;
+  // The prologue above reads only the weights.  Launched as a programmatic
+  // dependent of the previous kernel of the backward pass, this CTA waits for
+  // it here, before its first access to the states, adjoints, partial sums or
+  // flags, and lets the next launch start its own prologue as SMs free up.
+  griddep_wait();
+  griddep_launch_dependents();
 
   const int plane = nx * ny;
   const int tiles_x = (nx + WG_THREADS - 1) / WG_THREADS;
@@ -796,9 +802,22 @@ cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *
     attr_set = true;
   }
   if ((long long)g.nx * g.ny * g.batch * Q >= (1LL << 31)) return cudaErrorInvalidValue;
-  k_adjoint_tc<<<rows, THREADS, SMEM_BYTES, s>>>(state_n, lam_next, lam_out, g.nx, g.ny, g.batch,
-                                                 p, w, dw_partials, accumulate, timeout_flag);
-  return cudaGetLastError();
+  // a programmatic dependent of the previous kernel on the stream: in the
+  // backward pass that is always one of this library's (the push, a recompute
+  // step or the previous adjoint step), none of which writes the weights that
+  // the prologue reads before its wait
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)rows);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_adjoint_tc, state_n, lam_next, lam_out, g.nx, g.ny, g.batch, p,
+                            w, dw_partials, accumulate, timeout_flag);
 }
 
 }  // namespace lbm

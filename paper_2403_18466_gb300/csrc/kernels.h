@@ -74,11 +74,13 @@ cudaError_t launch_step_mlp_f32(const Grid &g, const float *in, float *out,
 // weights: FP32 (dtype 0) or BF16 (dtype 1), same packed row-major layout.
 // wait_limit: polls of each bounded mbarrier wait before the kernel gives up
 // and sets *timeout_flag (0 = the default, 2^20); max_ctas: cap on the
-// persistent grid (0 = one CTA per SM).
+// persistent grid (0 = one CTA per SM); chain: the previous operation on `s`
+// is this kernel with the same weights, so it is launched as a programmatic
+// dependent of it (its prologue overlaps that kernel's last tiles).
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wptr[6], int dtype,
                                  int *flag, int *timeout_flag, cudaStream_t s,
-                                 unsigned wait_limit = 0, int max_ctas = 0);
+                                 unsigned wait_limit = 0, int max_ctas = 0, bool chain = false);
 
 // Compiled layout of the tensor-core step: tile warpgroups per SM and, of
 // every 8 activation pairs, how many the XU evaluates.
@@ -98,7 +100,9 @@ cudaError_t launch_reduce_dw(const float *dw_partials, int rows, float *dW, cuda
 
 // adjoint_tc.cu ----------------------------------------------------------------
 // Tensor-core adjoint step (BF16 operands, FP32 accumulation); one partial row
-// per CTA (one persistent CTA per SM).
+// per CTA (one persistent CTA per SM).  Launched as a programmatic dependent
+// of the previous kernel on `s`, which must not write the weights `w` (its
+// prologue reads them before waiting for that kernel).
 int adjoint_tc_rows(const Grid &g, int sms);
 cudaError_t launch_adjoint_tc(const Grid &g, const float *state_n, const float *lam_next,
                               float *lam_out, const CollideParams &p, const MlpF32 &w,

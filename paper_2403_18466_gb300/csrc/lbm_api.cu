@@ -88,9 +88,12 @@ MlpF32 f32_view(const lbm_weights *w) {
   return m;
 }
 
-// One step from `in` to `out` with the given collision.
+// One step from `in` to `out` with the given collision.  `chain`: the previous
+// operation on the stream is a step of the same collision issued by the same
+// call (no copy or other kernel in between), so the tensor-core step may start
+// its prologue while that one finishes (programmatic dependent launch).
 cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind,
-                     const lbm_weights *w) {
+                     const lbm_weights *w, bool chain = false) {
   switch (kind) {
     case LBM_BGK: return lbm::launch_step_bgk(c->g, in, out, c->cp, c->d_flag, c->stream);
     case LBM_SMAG: return lbm::launch_step_smag(c->g, in, out, c->cp, c->d_flag, c->stream);
@@ -99,7 +102,8 @@ cudaError_t one_step(lbm_ctx *c, const float *in, float *out, lbm_collision kind
     case LBM_MLP_BF16: {
       const void *wp[6] = {w->w1, w->b1, w->w2, w->b2, w->w3, w->b3};
       return lbm::launch_step_mlp_bf16(c->g, in, out, c->cp, wp, w->dtype, c->d_flag,
-                                       c->d_flag + 1, c->stream, c->wait_limit, c->max_ctas);
+                                       c->d_flag + 1, c->stream, c->wait_limit, c->max_ctas,
+                                       chain);
     }
   }
   return cudaErrorInvalidValue;
@@ -246,7 +250,7 @@ int lbm_step(lbm_ctx *c, int n, lbm_collision kind, const lbm_weights *w) {
   const int wc = check_weights(kind, w);
   if (wc != LBM_OK) return wc;
   for (int s = 0; s < n; ++s) {
-    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w));
+    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w, s > 0));
     c->cur ^= 1;
   }
   return LBM_OK;
@@ -358,7 +362,7 @@ static int forward_record(lbm_ctx *c, lbm_collision kind, int n, int k, const lb
     if (s % k == 0)
       CUDA_TRY(cudaMemcpyAsync(base + (size_t)(s / k) * sb, c->buf[c->cur], sb,
                                cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w));
+    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w, s % k != 0));
     c->cur ^= 1;
   }
   if (n == 0)
@@ -410,7 +414,7 @@ static int backward(lbm_ctx *c, bool tc, const float *dL_df_final, const lbm_wei
     // recompute g^{s0+1} .. g^{s0+len-1} into seg[0 .. len-2]
     for (int j = 1; j < len; ++j) {
       const float *in = j == 1 ? ck : seg + (size_t)(j - 2) * sf;
-      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, kind, w));
+      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, kind, w, j > 1));
     }
     for (int j = len - 1; j >= 0; --j) {
       const float *gs = j == 0 ? ck : seg + (size_t)(j - 1) * sf;

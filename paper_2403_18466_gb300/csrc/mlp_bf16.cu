@@ -394,6 +394,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   T.b = (int)(t_begin / ((long long)tiles_x * ny));
   const float omega = p.omega;
 
+  // Everything above reads only the weights.  With programmatic dependent
+  // launch this CTA may be running while the previous step (which writes `in`
+  // and reads `out`) finishes on other SMs: wait for it before the first
+  // access to either state buffer, and let the next step start its own
+  // prologue as SMs free up (a CTA holds all of an SM's registers, so the
+  // next step's CTA becomes resident only after this one exits).
+  griddep_wait();
+  griddep_launch_dependents();
+
   uint32_t phase = 0;
   bool fail = false;  // the leader's last bounded wait gave up (leader only)
   bool bad = false;   // an unstable node was met (per thread)
@@ -560,7 +569,7 @@ cudaError_t launch_activation(const float *a, int n, int path, float *out, cudaS
 cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
                                  const CollideParams &p, const void *const wp[6], int dtype,
                                  int *flag, int *timeout_flag, cudaStream_t s,
-                                 unsigned wait_limit, int max_ctas) {
+                                 unsigned wait_limit, int max_ctas, bool chain) {
   static int sms = 0;
   static bool attr_done[2] = {false, false};
   if (!sms) {
@@ -581,10 +590,22 @@ cudaError_t launch_step_mlp_bf16(const Grid &g, const float *in, float *out,
   if (ctas > (long long)sms) ctas = sms;
   if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
   if (wait_limit == 0) wait_limit = DEFAULT_WAIT_LIMIT;
-  kern<<<(unsigned)ctas, THREADS, SMEM_BYTES, s>>>(in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1],
-                                                   wp[2], wp[3], wp[4], wp[5], flag, timeout_flag,
-                                                   wait_limit);
-  return cudaGetLastError();
+  // programmatic dependent launch after a step of this kernel (the prologue --
+  // weights to shared memory, tensor-memory allocation -- overlaps that step's
+  // last tiles); otherwise plain stream order, since the prologue reads the
+  // weights, which an earlier operation may still be writing
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chain ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, in, out, g.nx, g.ny, g.batch, p, wp[0], wp[1], wp[2],
+                            wp[3], wp[4], wp[5], flag, timeout_flag, wait_limit);
 }
 
 }  // namespace lbm

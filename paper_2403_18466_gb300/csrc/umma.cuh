@@ -226,6 +226,20 @@ __device__ __forceinline__ void fence_mbarrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// ---- programmatic dependent launch ---------------------------------------
+// A kernel launched with programmatic stream serialization may start while
+// the previous kernel in the stream is still finishing; griddep_wait() blocks
+// until that kernel has completed and its memory writes are visible (a no-op
+// for a kernel launched without the attribute).  griddep_launch_dependents()
+// lets the next such kernel be scheduled once every CTA of this grid has
+// issued it or exited.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- named barriers over a subset of warps --------------------------------
 __device__ __forceinline__ void named_barrier(uint32_t id, uint32_t nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
