@@ -18,6 +18,7 @@
 #include "approx.cuh"
 #include "kernels.h"
 #include "lattice.cuh"
+#include "umma.cuh"
 
 namespace lbm {
 namespace {
@@ -89,6 +90,8 @@ template <int KIND>
 __global__ void __launch_bounds__(VEC_THREADS)
     k_step_vec(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
                CollideParams p, int *flag) {
+  umma::griddep_wait();  // launched as a dependent of the previous step
+  umma::griddep_launch_dependents();
   const int lane = threadIdx.x & 31;
   const int x0 = (blockIdx.x * VEC_THREADS + threadIdx.x) * 4;
   const int y = blockIdx.y;
@@ -144,6 +147,8 @@ template <int KIND>
 __global__ void __launch_bounds__(SCALAR_THREADS)
     k_step_scalar(const float *__restrict__ in, float *__restrict__ out, int nx, int ny,
                   CollideParams p, int *flag) {
+  umma::griddep_wait();  // launched as a dependent of the previous step
+  umma::griddep_launch_dependents();
   const int x = blockIdx.x * SCALAR_THREADS + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= nx) return;
@@ -158,17 +163,25 @@ __global__ void __launch_bounds__(SCALAR_THREADS)
   for (int i = 0; i < Q; ++i) ob[i * plane + (size_t)y * nx + x] = d[i];
 }
 
+// Programmatic dependent launch: the kernel waits for the previous kernel on
+// the stream before its first global access, so its CTAs may be scheduled
+// while that kernel's last CTAs finish (it hides the launch gap between steps).
 template <int KIND>
 cudaError_t launch_step(const Grid &g, const float *in, float *out, const CollideParams &p,
                         int *flag, cudaStream_t s) {
-  if (g.nx % 4 == 0) {
-    dim3 grid((g.nx / 4 + VEC_THREADS - 1) / VEC_THREADS, g.ny, g.batch);
-    k_step_vec<KIND><<<grid, VEC_THREADS, 0, s>>>(in, out, g.nx, g.ny, p, flag);
-  } else {
-    dim3 grid((g.nx + SCALAR_THREADS - 1) / SCALAR_THREADS, g.ny, g.batch);
-    k_step_scalar<KIND><<<grid, SCALAR_THREADS, 0, s>>>(in, out, g.nx, g.ny, p, flag);
-  }
-  return cudaGetLastError();
+  const bool vec = g.nx % 4 == 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = vec ? dim3((g.nx / 4 + VEC_THREADS - 1) / VEC_THREADS, g.ny, g.batch)
+                    : dim3((g.nx + SCALAR_THREADS - 1) / SCALAR_THREADS, g.ny, g.batch);
+  cfg.blockDim = dim3(vec ? VEC_THREADS : SCALAR_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (vec) return cudaLaunchKernelEx(&cfg, k_step_vec<KIND>, in, out, g.nx, g.ny, p, flag);
+  return cudaLaunchKernelEx(&cfg, k_step_scalar<KIND>, in, out, g.nx, g.ny, p, flag);
 }
 
 // ---------------------------------------------------------------------------
