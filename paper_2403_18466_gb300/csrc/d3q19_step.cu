@@ -14,6 +14,7 @@
 // outputs for all 32 nodes, reading weight rows with warp-uniform loads.
 #include "d3q19.cuh"
 #include "kernels3d.h"
+#include "umma.cuh"
 
 namespace lbm {
 namespace d3 {
@@ -69,6 +70,8 @@ __device__ __forceinline__ void flag_bad(bool bad, int *flag) {
 template <int KIND>
 __global__ void __launch_bounds__(NT) k3_step(const float *__restrict__ in, float *__restrict__ out,
                                               Grid3 g, Collide3 c, int *flag) {
+  umma::griddep_wait();  // launched as a dependent of the previous step
+  umma::griddep_launch_dependents();
   Pos p;
   if (!node_pos(g, p)) return;
   float d[Q], deq[Q];
@@ -255,13 +258,21 @@ dim3 node_grid(const Grid3 &g) { return dim3((g.nx + NT - 1) / NT, g.ny, g.nz * 
 
 }  // namespace
 
+// Programmatic dependent launch: the kernel waits for the previous kernel on
+// the stream before its first global access, which hides the launch gap.
 cudaError_t launch_step(const Grid3 &g, const float *in, float *out, const Collide3 &c, int kind,
                         int *flag, cudaStream_t s) {
-  if (kind == KIND_SMAG)
-    k3_step<KIND_SMAG><<<node_grid(g), NT, 0, s>>>(in, out, g, c, flag);
-  else
-    k3_step<KIND_BGK><<<node_grid(g), NT, 0, s>>>(in, out, g, c, flag);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = node_grid(g);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (kind == KIND_SMAG) return cudaLaunchKernelEx(&cfg, k3_step<KIND_SMAG>, in, out, g, c, flag);
+  return cudaLaunchKernelEx(&cfg, k3_step<KIND_BGK>, in, out, g, c, flag);
 }
 
 size_t mlp_f32_smem_bytes() { return sizeof(MlpSmem); }
