@@ -332,3 +332,49 @@ def test_bounded_wait_timeout_and_recovery(lbm):
     b.step(2, "mlp_bf16", w)
     assert a.status() == lbm.LBM_OK and b.status() == lbm.LBM_OK
     assert torch.equal(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("kind", ["mlp_bf16", "bgk", "smag"])
+def test_steps_in_one_call_equal_single_step_calls(lbm, kind):
+    """Within one lbm_step call every step after the first is a programmatic
+    dependent launch (its prologue overlaps the previous step, and it waits for
+    that step before touching the states); each call's first step is ordered
+    normally.  Six steps in one call must therefore be bitwise the six steps of
+    six calls -- on a lattice large enough that every warpgroup walks many
+    tiles and the CTAs of consecutive steps overlap."""
+    nx, ny, B = 1024, 512, 2
+    w = lbm.weights_struct(_dev(_theta(14)))
+    f = _dev(population_field(B, ny, nx, seed=33))
+    a = lbm.Lattice(nx, ny, B, tau=0.55, smag_cs=0.1, force_amp=1e-5, force_mode=2, device=DEV)
+    b = lbm.Lattice(nx, ny, B, tau=0.55, smag_cs=0.1, force_amp=1e-5, force_mode=2, device=DEV)
+    a.set_state(f)
+    b.set_state(f)
+    a.step(6, kind, w)
+    for _ in range(6):
+        b.step(1, kind, w)
+    assert a.status() == lbm.LBM_OK and b.status() == lbm.LBM_OK
+    assert torch.equal(a.get_state(), b.get_state())
+
+
+def test_weights_written_just_before_a_call_are_used(lbm):
+    """The first tensor-core step of a call is launched in plain stream order
+    because its prologue reads the weights before it waits: weights that a
+    device kernel writes on the same stream just before the call (as an
+    optimizer step does) are the ones the whole call uses."""
+    nx, ny = 2048, 256
+    th_a, th_b = _dev(_theta(15)), _dev(_theta(16))
+    f = _dev(population_field(1, ny, nx, seed=35))
+    ref = lbm.Lattice(nx, ny, 1, tau=0.6, device=DEV)
+    ref.set_state(f)
+    ref.step(4, "mlp_bf16", lbm.weights_struct(th_b))
+    lat = lbm.Lattice(nx, ny, 1, tau=0.6, device=DEV)
+    theta = th_a.clone()
+    w = lbm.weights_struct(theta)
+    lat.set_state(f)
+    lat.step(2, "mlp_bf16", w)        # a call that reads the old weights
+    lat.set_state(f)
+    big = torch.empty(1 << 26, device=DEV)
+    big.normal_()                     # keeps the stream busy ...
+    theta.copy_(th_b)                 # ... then overwrites the weights in place
+    lat.step(4, "mlp_bf16", w)        # no host synchronisation in between
+    assert torch.equal(lat.get_state(), ref.get_state())
