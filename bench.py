@@ -426,6 +426,28 @@ def _time_training(lbm, torch, dev, inputs):
                      "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
     out["ratio_bf16_fwd_adj_over_f32_fwd"] = round(
         out["bf16"]["fwd_adj_ms_per_step"] / out["f32"]["fwd_ms_per_step"], 3)
+    # the memory / recompute trade of the checkpoint interval k (tensor-core
+    # pair, same 16-step unroll): the backward recomputes (k - 1)/k of a
+    # forward step per step and the workspace holds ceil(16/k) + k + 1 states
+    sweep = {}
+    for ck_i in (1, 2, 4, 8):
+        ws_i = torch.empty(lat.record_bytes(L, ck_i) // 4, dtype=torch.float32, device=dev)
+        for rep in range(3):
+            lat.set_state(f0)
+            ev[0].record()
+            lat.forward_record(L, ck_i, w, ws_i, "bf16")
+            ev[1].record()
+            loss, g = lat.velocity_loss(ux, uy)
+            lat.backward(g, w, ws_i, dW, None, "bf16")
+            ev[2].record()
+            ev[2].synchronize()
+            res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
+        sweep[str(ck_i)] = {"fwd_ms_per_step": round(res["fwd_ms"] / L, 4),
+                            "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / L, 4),
+                            "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
+                            "workspace_mb": round(ws_i.numel() * 4 / 2**20, 1)}
+        del ws_i
+    out["bf16_checkpoint_every"] = sweep
     # the paper's training variant: population loss (Eq. S13) on |S| = 512
     # random nodes after L_T = 12 or 24 unrolled steps, tensor-core pair
     gen = torch.Generator().manual_seed(11)
