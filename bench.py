@@ -720,10 +720,23 @@ def run_profile_case(args):
         sys.exit(1)
 
 
+def kernel_code_digest(kernel_sources):
+    """SHA-256 of the kernel sources with // comments and blank lines removed,
+    so that a comment edit does not void a capture but any code change does."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in kernel_sources:
+        with open(os.path.join(ROOT, "paper_2403_18466_gb300", "csrc", src)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip() if '"' not in line else line.rstrip()
+                if code.strip():
+                    h.update((code + "\n").encode())
+    return h.hexdigest()
+
+
 def _traffic_from_profile(kernel_sources, summary, nodes):
     """DRAM bytes per launch of the step kernel from a committed ncu summary,
-    scaled to `nodes`; None if the kernel sources changed since the capture."""
-    import hashlib
+    scaled to `nodes`; None if the kernel code changed since the capture."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         fields = {}
@@ -731,10 +744,7 @@ def _traffic_from_profile(kernel_sources, summary, nodes):
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
-        h = hashlib.sha256()
-        for src in kernel_sources:
-            h.update(open(os.path.join(ROOT, "paper_2403_18466_gb300", "csrc", src), "rb").read())
-        if fields.get("source_sha256") != h.hexdigest():
+        if fields.get("code_sha256") != kernel_code_digest(kernel_sources):
             return None
         return float(fields["dram_bytes_per_launch"]) * nodes / float(fields["nodes_per_launch"])
     except Exception:

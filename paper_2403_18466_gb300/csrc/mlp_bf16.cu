@@ -42,7 +42,8 @@
 // The FMA form takes ~26 cycles per warp-wide pair in isolation against 16.4
 // for the XU form, and 13 issue slots against 2, so it pays only as a small
 // share next to the kernel's other work (measured at 4096^2: 8 of 8 pairs on
-// the XU 25.2 G nodes/s, 7 of 8: 25.3 G, 6: 25.1 G, 4: 20.3 G).
+// the XU 26.2 G nodes/s, 7 of 8: 26.5 G, 6: 25.8 G; 4 of 8, in an earlier
+// form of the kernel: 20.3 G against 25.3 G for 7 of 8).
 //
 // Per node the moments, equilibrium, x and the BGK + force update are
 // computed once, while the previous tile's last GEMM runs; the epilogue of
@@ -56,6 +57,11 @@
 // the whole warpgroup at once: it leaves the loop, the leader sets the timeout
 // flag and drains its outstanding commit (full limit), and tensor memory is
 // always freed.
+//
+// Consecutive steps of one call are programmatic dependent launches: a step's
+// prologue (weights to shared memory, tensor-memory allocation) runs on the
+// SMs that the previous step has already left, and griddepcontrol.wait holds
+// it back from the state buffers until that step has completed.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
