@@ -198,13 +198,21 @@ __device__ __forceinline__ void drain_cols(uint32_t tm_row) {
   uint32_t p[NCOL / 2];
 #pragma unroll
   for (int e = 0; e < NCOL / 2; ++e) {
-    float h[2];
+    const int k = C0 + 2 * e;
+    if (k + 1 < KVALID) {
+      // LeakyReLU of both values: the two products 0.01 v in one packed
+      // multiply (round to nearest per lane, as the scalar form), then max
+      const float a0 = __uint_as_float(v[2 * e]), a1 = __uint_as_float(v[2 * e + 1]);
+      const float2 s = __fmul2_rn(make_float2(a0, a1), make_float2(LEAKY, LEAKY));
+      p[e] = pack2(fmaxf(a0, s.x), fmaxf(a1, s.y));
+    } else {
+      float h[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int k = C0 + 2 * e + j;
-      h[j] = k < KVALID ? lrelu(__uint_as_float(v[2 * e + j])) : (k == KVALID ? 1.0f : 0.0f);
+      for (int j = 0; j < 2; ++j)
+        h[j] = k + j < KVALID ? lrelu(__uint_as_float(v[2 * e + j]))
+                              : (k + j == KVALID ? 1.0f : 0.0f);
+      p[e] = pack2(h[0], h[1]);
     }
-    p[e] = pack2(h[0], h[1]);
   }
 #pragma unroll
   for (int q = 0; q < NCOL / 32; ++q)
