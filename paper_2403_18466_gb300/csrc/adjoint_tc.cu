@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   volatile int *err = &S.err;
 
-  // ---- prologue: weights in the six operand layouts
+  // ---- prologue: weights in the five operand layouts, and b3
   for (int e = tid; e < HIDDEN * K1; e += THREADS) {
     const int n = e / K1, k = e % K1;
     store_bf16(S.w1, n, k, K1, k < 9 ? w.w1[n * 9 + k] : (k == 9 ? w.b1[n] : 0.f));
