@@ -220,6 +220,33 @@ def test_zero_output_layer_equals_bgk_bitwise(lbm):
         assert torch.equal(a.get_state(), b.get_state())
 
 
+@pytest.mark.parametrize("kind", ["mlp_bf16", "mlp_f32"])
+def test_output_in_conserved_span_is_bgk(lbm, kind):
+    """An output o in span{1, c_x, c_y} carries no mass or momentum change that
+    the projection of Eqs. S11-S12 could keep: P o = 0, so the learned step is
+    BGK.  Zero output weights and b3 = 0.25 - 0.125 c_x + 0.0625 c_y (values
+    exact in bf16, so the tensor-core path sees the same vector) with non-zero
+    hidden layers; tolerance: FP32 rounding of the projection (1e-6 of w_i after
+    three steps), against a correction of (rho/tau) * 0.3 if P were wrong."""
+    from gpu_helpers import weighted_pop_err
+    theta = _theta(17)
+    W1, b1, W2, b2, W3, b3 = inputs.unpack_mlp(theta)
+    cxv, cyv, _ = oracle.lattice()
+    W3[:] = 0.0
+    b3[:] = 0.25 - 0.125 * cxv + 0.0625 * cyv
+    for nx, ny in ((256, 32), (100, 7)):
+        f = population_field(1, ny, nx, seed=3)
+        a = lbm.Lattice(nx, ny, 1, tau=0.6, force_amp=1e-4, force_mode=2, device=DEV)
+        b = lbm.Lattice(nx, ny, 1, tau=0.6, force_amp=1e-4, force_mode=2, device=DEV)
+        a.set_state(_dev(f))
+        b.set_state(_dev(f))
+        a.step(3, kind, lbm.weights_struct(_dev(theta)))
+        b.step(3, "bgk")
+        err = weighted_pop_err(_np(a.get_state()), _np(b.get_state()))
+        print(f"{kind} {nx}x{ny}: span output vs BGK {err:.3e} of w_i")
+        assert err <= 1e-6, err
+
+
 def test_bf16_weight_input_matches_f32_input(lbm):
     theta = bf16_round(_theta(6))  # exactly representable in bf16
     f = population_field(1, 40, 300, seed=5)
