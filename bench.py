@@ -243,6 +243,34 @@ def _time_steps(lat, kind, w, steps, torch, stream):
     return start.elapsed_time(end)  # ms
 
 
+def _time_diagnostics(lat, n, torch, stream, hbm_peak):
+    """On-device turbulence diagnostics of the n^2 state (the paper's
+    evaluation quantities): the energy spectrum (velocity from the moments, one
+    batched cuFFT R2C of both components, shell binning) and the longitudinal
+    structure functions S^p(r), p = 1..6, r = 1..256 (u read once per
+    separation: 8 B per node per r of algorithmic traffic)."""
+    kmax, rmax = n // 2, 256
+    out = {}
+    for name, fn in (("energy_spectrum", lambda: lat.energy_spectrum(kmax)),
+                     ("structure_functions_r256", lambda: lat.structure_functions(rmax))):
+        fn()
+        torch.cuda.synchronize()
+        reps = 5
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        out[name] = {"ms": round(a.elapsed_time(b) / reps, 3)}
+    sf = out["structure_functions_r256"]
+    g = 8.0 * n * n * rmax / (sf["ms"] * 1e-3) / 1e9
+    sf["gbs"] = round(g, 1)
+    sf["hbm_frac"] = round(g / hbm_peak, 4)
+    out["grid"] = f"{n}x{n}"
+    return out
+
+
 def _time_steps_segments(lat, kind, w, steps, torch, stream, nseg=5):
     """The same timed region as _time_steps, issued as nseg back-to-back
     segments with an event between them (events do not stall the stream).
@@ -359,6 +387,7 @@ def run_gpu(args):
                                  "status": lbm.lbm_strerror(lat_t.status())}
     del lat_t
     comps["training"] = _time_training(lbm, torch, dev, inputs)
+    comps["diagnostics"] = _time_diagnostics(lat, N_GRID, torch, stream, hbm_peak)
     comps["d3q19"] = _time_d3q19(lbm, torch, dev, inputs, hbm_peak)
     del lat
     torch.cuda.empty_cache()
