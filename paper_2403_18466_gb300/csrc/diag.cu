@@ -4,9 +4,12 @@
 //
 // Structure functions: S^p(r) = < [(u(x + r e) - u(x)) . e]^p >, p = 1..6,
 // r = 1..rmax, averaged over every node and the two lattice directions
-// e = x^, y^ (periodic).  One block per (r, chunk of rows); per-thread FP32
-// sums over at most 32 nodes are flushed into FP64 accumulators; per-block
-// partials are added in a fixed order, so results are reproducible.
+// e = x^, y^ (periodic).  For rmax <= 256: row segments and column strips of
+// the field staged in shared memory with an rmax halo, one thread per
+// separation; otherwise one block per (r, chunk of rows).  Either way
+// per-thread FP32 sums over at most 32 nodes are flushed into FP64
+// accumulators and per-block partials are added in a fixed order, so results
+// are reproducible.
 //
 // Energy spectrum: E(k) = 1/2 sum_{round(|k'|) = k} |u_hat(k')|^2 / N^2 for the
 // unnormalised 2D DFT (N = nx ny), averaged over the batch, so that the sum
@@ -79,6 +82,132 @@ __global__ void __launch_bounds__(SF_THREADS)
     part[((size_t)(r - 1) * gridDim.y + chunk) * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// Tiled form for rmax <= SFT_R (the usual case): one pass over the field per
+// direction instead of one per separation.  Thread r - 1 of a block owns
+// separation r; the block stages a periodic segment of the field with an rmax
+// halo in shared memory, and for every node of it thread r takes
+// s[x + r] - s[x] (the first read is a broadcast, the second conflict-free).
+// Each thread sums at most 32 terms in FP32 before adding them to its FP64
+// sums; each block writes its 6 sums per separation; a last kernel adds the
+// blocks in a fixed order.
+constexpr int SFT_R = 256;   // separations per block (threads)
+constexpr int SFT_X = 1024;  // nodes of a row segment (x direction)
+constexpr int SFT_RB = 16;   // rows per x block
+constexpr int SFT_C = 32;    // columns of a y strip
+constexpr int SFT_Y = 256;   // rows of a y strip
+constexpr int SFT_CS = SFT_C + 1;  // padded column stride
+
+struct SfAcc {
+  double acc[6];
+  float facc[6];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      acc[p] = 0.0;
+      facc[p] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(float d) {
+    const float d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
+    facc[0] += d;
+    facc[1] += d2;
+    facc[2] += d3;
+    facc[3] += d4;
+    facc[4] += d4 * d;
+    facc[5] += d3 * d3;
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      acc[p] += (double)facc[p];
+      facc[p] = 0.f;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(SFT_R)
+    k_sf_rows(const float *__restrict__ ux, int nx, int rows, int rmax, double *__restrict__ part) {
+  extern __shared__ float seg[];  // SFT_X + rmax
+  const int x0 = blockIdx.x * SFT_X;
+  const int w = min(SFT_X, nx - x0);
+  const int row0 = blockIdx.y * SFT_RB, row1 = min(row0 + SFT_RB, rows);
+  const int r = threadIdx.x + 1;
+  SfAcc a;
+  a.zero();
+  for (int row = row0; row < row1; ++row) {
+    const float *u = ux + (size_t)row * nx;  // row b ny + y of the [B][ny][nx] field
+    __syncthreads();
+    for (int i = threadIdx.x; i < w + rmax; i += SFT_R) seg[i] = u[(x0 + i) % nx];
+    __syncthreads();
+    if (r <= rmax) {
+      for (int xb = 0; xb < w; xb += 32) {
+        const int xe = min(xb + 32, w);
+        for (int x = xb; x < xe; ++x) a.add(seg[x + r] - seg[x]);
+        a.flush();
+      }
+    }
+  }
+  if (r <= rmax) {
+    double *o = part + ((size_t)(blockIdx.y * gridDim.x + blockIdx.x) * rmax + (r - 1)) * 6;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) o[p] = a.acc[p];
+  }
+}
+
+__global__ void __launch_bounds__(SFT_R)
+    k_sf_cols(const float *__restrict__ uy, int nx, int ny, int rmax, size_t part_off,
+              double *__restrict__ part) {
+  extern __shared__ float strip[];  // (SFT_Y + rmax) rows x SFT_CS
+  const int x0 = blockIdx.x * SFT_C, cw = min(SFT_C, nx - x0);
+  const int y0 = blockIdx.y * SFT_Y, h = min(SFT_Y, ny - y0);
+  const float *u = uy + (size_t)blockIdx.z * nx * ny;
+  for (int e = threadIdx.x; e < (h + rmax) * SFT_C; e += SFT_R) {
+    const int j = e / SFT_C, c = e % SFT_C;
+    if (c < cw) strip[j * SFT_CS + c] = u[(size_t)((y0 + j) % ny) * nx + x0 + c];
+  }
+  __syncthreads();
+  const int r = threadIdx.x + 1;
+  SfAcc a;
+  a.zero();
+  if (r <= rmax) {
+    for (int j = 0; j < h; ++j) {
+      const float *s0 = strip + j * SFT_CS, *s1 = strip + (j + r) * SFT_CS;
+      for (int c = 0; c < cw; ++c) a.add(s1[c] - s0[c]);
+      a.flush();
+    }
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double *o = part + ((part_off + blk) * rmax + (r - 1)) * 6;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) o[p] = a.acc[p];
+  }
+}
+
+// S[p][r] = sum over the blocks of the tiled form (in order) / (2 B N)
+__global__ void k_sf_final(const double *__restrict__ part, int rmax, int blocks,
+                           double inv_count, double *__restrict__ S) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6 * rmax) return;
+  const int p = e / rmax, r = e % rmax;
+  double s = 0.0;
+  for (int k = 0; k < blocks; ++k) s += part[((size_t)k * rmax + r) * 6 + p];
+  S[e] = s * inv_count;
+}
+
+struct SfTiles {
+  int xb, yb;  // blocks along x and y of the row kernel; of the column kernel: bx, by, bz
+  int cx, cy, cz;
+  __host__ int total() const { return xb * yb + cx * cy * cz; }
+};
+SfTiles sf_tiles(const Grid &g) {
+  SfTiles t;
+  t.xb = (g.nx + SFT_X - 1) / SFT_X;
+  t.yb = (g.ny * g.batch + SFT_RB - 1) / SFT_RB;
+  t.cx = (g.nx + SFT_C - 1) / SFT_C;
+  t.cy = (g.ny + SFT_Y - 1) / SFT_Y;
+  t.cz = g.batch;
+  return t;
+}
+
 // S[p][r] = sum over chunks (in order) / (2 B N)
 __global__ void k_structure_final(const double *__restrict__ part, int rmax, int chunks,
                                   double inv_count, double *__restrict__ S) {
@@ -137,7 +266,14 @@ __global__ void k_spectrum_final(const double *__restrict__ rowpart, int ny, int
 
 }  // namespace
 
+// The tiled form applies for rmax <= SFT_R and grids within its launch limits.
+static bool sf_tiled(const Grid &g, int rmax) {
+  const SfTiles t = sf_tiles(g);
+  return rmax <= SFT_R && t.yb <= 65535 && t.cy <= 65535 && t.cz <= 65535;
+}
+
 size_t structure_partials_doubles(const Grid &g, int rmax) {
+  if (sf_tiled(g, rmax)) return (size_t)sf_tiles(g).total() * rmax * 6;
   const int rows = g.ny * g.batch;
   const int rpb = 8;
   const int chunks = (rows + rpb - 1) / rpb;
@@ -146,6 +282,28 @@ size_t structure_partials_doubles(const Grid &g, int rmax) {
 
 cudaError_t launch_structure_functions(const Grid &g, const float *ux, const float *uy, int rmax,
                                        double *part, double *S, cudaStream_t s) {
+  if (sf_tiled(g, rmax)) {
+    const SfTiles t = sf_tiles(g);
+    const size_t smem_cols = sizeof(float) * (size_t)(SFT_Y + rmax) * SFT_CS;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_sf_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(float) * (SFT_Y + SFT_R) * SFT_CS));
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    k_sf_rows<<<dim3(t.xb, t.yb), SFT_R, sizeof(float) * (SFT_X + rmax), s>>>(
+        ux, g.nx, g.ny * g.batch, rmax, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sf_cols<<<dim3(t.cx, t.cy, t.cz), SFT_R, smem_cols, s>>>(uy, g.nx, g.ny, rmax,
+                                                              (size_t)t.xb * t.yb, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sf_final<<<(6 * rmax + 255) / 256, 256, 0, s>>>(part, rmax, t.total(),
+                                                      1.0 / (2.0 * (double)g.nodes()), S);
+    return cudaGetLastError();
+  }
   const int rows = g.ny * g.batch;
   const int rpb = 8;
   const int chunks = (rows + rpb - 1) / rpb;
