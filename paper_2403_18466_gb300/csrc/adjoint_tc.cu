@@ -69,9 +69,9 @@ constexpr uint32_t WAIT_LIMIT = 1u << 20;
 enum { ST_DW3 = 0, ST_DW2 = 1, ST_DW1 = 2, STAGES = 3 };
 
 struct __align__(16) WgBuffers {
-  unsigned char a1[128 * K1 * 2];   // x | 1 | 0        (node rows)
+  unsigned char a1[2][128 * K1 * 2];  // x | 1 | 0 (node rows), alternate tiles
   unsigned char h1[128 * K2 * 2];   // h1 | 1 | 0
-  unsigned char h2[128 * K2 * 2];   // h2 | 1 | 0, then dL/da1 (row length 64)
+  unsigned char h2[128 * 64 * 2];   // h2, then dL/da1
   unsigned char ob[128 * 16 * 2];   // dL/do | 0
   unsigned char a2b[128 * 64 * 2];  // dL/da2
 };
@@ -253,7 +253,7 @@ __device__ __forceinline__ void park_row(uint32_t tm, unsigned char *g, int r) {
 }
 
 // Layer-2 epilogue with the reverse step fused: h2 = tanh(D) as the bf16 row
-// r of `hdst` (the dW3 operand), and with g = dL/dh2 from the bf16 row r of
+// r of `hdst` (row length 64, the dW3 operand), and with g = dL/dh2 from the bf16 row r of
 // `g`, dL/da2 = g (1 - h2^2) written back over g.  Returns sum_k g_k h2_k
 // (h2 as stored), the output's term of the rho-derivative before its 1/rho.
 __device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *hdst,
@@ -280,7 +280,7 @@ __device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *h
         dot0 = fmaf(g0, bf16_lo(hp[q]), dot0);
         dot1 = fmaf(g1, bf16_hi(hp[q]), dot1);
       }
-      *reinterpret_cast<uint4 *>(hdst + canon_offset(r, c + 8 * e, K2)) =
+      *reinterpret_cast<uint4 *>(hdst + canon_offset(r, c + 8 * e, 64)) =
           make_uint4(hp[0], hp[1], hp[2], hp[3]);
       *reinterpret_cast<uint4 *>(g + canon_offset(r, c + 8 * e, 64)) =
           make_uint4(ap[0], ap[1], ap[2], ap[3]);
@@ -367,13 +367,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     store_bf16(S.w1t, i, j, 64, i < 9 ? w.w1[j * 9 + i] : 0.f);
   }
   if (warp < DW_WARP) {
-    // constant columns 64..79 of the h1 / h2 rows: 1, 0, ..., 0
+    // constant columns 64..79 of the h1 rows: 1, 0, ..., 0
     WgBuffers &B = S.wb[warp >> 2];
     const int r = tid & 127;
-    for (unsigned char *hb : {B.h1, B.h2}) {
-      *reinterpret_cast<uint4 *>(hb + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4 *>(hb + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
-    }
+    *reinterpret_cast<uint4 *>(B.h1 + canon_offset(r, 64, K2)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(B.h1 + canon_offset(r, 72, K2)) = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
     for (int g = 0; g < WGS; ++g) {
@@ -452,11 +450,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           // (dL/da1 lives in the h2 buffer)
           uint32_t sa, sb, a_lbo, b_lbo;
           if (s == ST_DW3) {
-            sa = smem_u32(B.h2), a_lbo = 1280, sb = smem_u32(B.ob), b_lbo = 256;
+            sa = smem_u32(B.h2), a_lbo = 1024, sb = smem_u32(B.ob), b_lbo = 256;
           } else if (s == ST_DW2) {
             sa = smem_u32(B.a2b), a_lbo = 1024, sb = smem_u32(B.h1), b_lbo = 1280;
           } else {
-            sa = smem_u32(B.h2), a_lbo = 1024, sb = smem_u32(B.a1), b_lbo = 256;
+            sa = smem_u32(B.h2), a_lbo = 1024, sb = smem_u32(B.a1[k & 1]), b_lbo = 256;
           }
 #pragma unroll
           for (int q = 0; q < 8; ++q)
@@ -477,14 +475,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- tile warpgroups
     const int wg = warp >> 2;
     const int r = tid & 127;
-    const bool leader = r == 0;
+#ifndef LBM_ADJ_LEADER_SPREAD
+#define LBM_ADJ_LEADER_SPREAD 1
+#endif
+    // the thread that issues and waits for the warpgroup's GEMMs
+    const bool leader = LBM_ADJ_LEADER_SPREAD ? r == 32 * ((wg + 1) & 3) : r == 0;
     const uint32_t bar_id = 1 + wg;
     WgBuffers &B = S.wb[wg];
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t tm_wg = tmem + (uint32_t)(wg * WG_COLS);
     const uint32_t tm_row = tm_wg + C_D + lane_off;
     const uint32_t bar = smem_u32(&S.bar[wg]);
-    const uint32_t s_a1 = smem_u32(B.a1), s_h1 = smem_u32(B.h1), s_h2 = smem_u32(B.h2);
+    const uint32_t s_h1 = smem_u32(B.h1), s_h2 = smem_u32(B.h2);
     const uint32_t s_ob = smem_u32(B.ob), s_a2b = smem_u32(B.a2b);
     const uint32_t s_w1 = smem_u32(S.w1), s_w2 = smem_u32(S.w2);
     const uint32_t s_w3t = smem_u32(S.w3t), s_w2t = smem_u32(S.w2t), s_w1t = smem_u32(S.w1t);
@@ -513,14 +515,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   named_barrier(bar_id, WG_THREADS);
 
     for (int it = 0; it < count; ++it) {
-      // the previous tile's dW2 and dW1 GEMMs read a1, h1, h2 and dL/da2
-      if (it > 0) {
-        if (!wg_wait(smem_u32(&S.dwd[wg][ST_DW2]), (dpar >> ST_DW2) & 1u,
-                     smem_u32(&S.dwd[wg][ST_DW1]), (dpar >> ST_DW1) & 1u, true, leader, bar_id,
-                     err))
-          break;
-        dpar ^= (1u << ST_DW2) | (1u << ST_DW1);
-      }
+      // The previous tile's weight-gradient GEMMs may still be reading its
+      // buffers: dW2 reads h1 and dL/da2 (waited for before this tile's
+      // layer-1 epilogue writes them), dW1 reads its x and dL/da1 (x
+      // alternates between two buffers; dL/da1 shares the h2 buffer, waited
+      // for before the layer-2 epilogue).  dW3 was waited for within that tile.
+      unsigned char *a1 = B.a1[it & 1];
+      const uint32_t s_a1 = smem_u32(a1);
       const int x = T.x0 + r;
       const bool active = x < nx;
       const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
@@ -579,10 +580,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         shifted_feq(m, deq);
 #pragma unroll
         for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
-        *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 0, K1)) =
+        *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 0, K1)) =
             make_uint4(pack_bf16x2(xin[0], xin[1]), pack_bf16x2(xin[2], xin[3]),
                        pack_bf16x2(xin[4], xin[5]), pack_bf16x2(xin[6], xin[7]));
-        *reinterpret_cast<uint4 *>(B.a1 + canon_offset(r, 8, K1)) =
+        *reinterpret_cast<uint4 *>(a1 + canon_offset(r, 8, K1)) =
             make_uint4(pack_bf16x2(xin[8], 1.0f), 0u, 0u, 0u);
       }
       // ---- dL/do (FP32) needs only the incoming adjoint and rho, so its GEMM
@@ -631,7 +632,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         mma_commit(bar);
         pending = true;
       }
-      WAIT_OWN_OR_BREAK()
+      // own GEMMs, and the previous tile's dW2 (it reads h1 and dL/da2)
+      if (!wg_wait(bar, phase, smem_u32(&S.dwd[wg][ST_DW2]), (dpar >> ST_DW2) & 1u, it > 0, leader,
+                   bar_id, err))
+        break;
+      phase ^= 1;
+      pending = false;
+      if (it > 0) dpar ^= 1u << ST_DW2;
       park_row(tm_wg + C_DH1 + lane_off, B.a2b, r);  // read before the derivative overwrites it
       tanh_row(tm_row, B.h1, r, tm_wg + C_DH1 + lane_off);
       OPERANDS_READY()
@@ -644,7 +651,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         mma_commit(bar);
         pending = true;
       }
-      WAIT_OWN_OR_BREAK()
+      // own GEMM, and the previous tile's dW1 (it reads dL/da1 in the h2 buffer)
+      if (!wg_wait(bar, phase, smem_u32(&S.dwd[wg][ST_DW1]), (dpar >> ST_DW1) & 1u, it > 0, leader,
+                   bar_id, err))
+        break;
+      phase ^= 1;
+      pending = false;
+      if (it > 0) dpar ^= 1u << ST_DW1;
       rhob = fmaf(tanh_grad_row(tm_row, B.h2, B.a2b, r) + ob_b3, inv_rho, rhob);
       OPERANDS_READY()
       if (leader) {
