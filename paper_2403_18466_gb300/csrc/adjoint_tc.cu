@@ -182,6 +182,19 @@ __device__ __forceinline__ void tanh_and_slope(float a, float &h, float &dh) {
   }
 }
 
+// Two units at once: h = tanh(a) per value, and 1 - h^2 for both in one
+// packed fused multiply-add (the same rounding as two scalar ones).
+__device__ __forceinline__ void tanh_and_slope2(float a0, float a1, float2 &h, float2 &dh) {
+  if (LBM_ADJ_TANH_EX2) {
+    tanh_and_slope(a0, h.x, dh.x);
+    tanh_and_slope(a1, h.y, dh.y);
+  } else {
+    asm("tanh.approx.f32 %0, %1;" : "=f"(h.x) : "f"(a0));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(h.y) : "f"(a1));
+    dh = __ffma2_rn(make_float2(-h.x, -h.y), h, make_float2(1.0f, 1.0f));
+  }
+}
+
 // D (64 FP32 columns of this thread's row) -> h = tanh(D) in FP32 -> bf16 row of
 // `dst` (K columns 0..63, the next GEMM's operand), and the derivative 1 - h^2,
 // computed to a few ulp in FP32 and rounded to bf16 pairs, into 32 TMEM
@@ -197,11 +210,10 @@ __device__ __forceinline__ void tanh_row(uint32_t tm_row, unsigned char *dst, in
     uint32_t p[16], q[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      float h0, h1, d0, d1;
-      tanh_and_slope(__uint_as_float(v[2 * e]), h0, d0);
-      tanh_and_slope(__uint_as_float(v[2 * e + 1]), h1, d1);
-      p[e] = pack_bf16x2(h0, h1);
-      q[e] = pack_bf16x2(d0, d1);
+      float2 h, dh;
+      tanh_and_slope2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]), h, dh);
+      p[e] = pack_bf16x2(h.x, h.y);
+      q[e] = pack_bf16x2(dh.x, dh.y);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
@@ -224,9 +236,12 @@ __device__ __forceinline__ void dtanh_row(uint32_t tm_row, uint32_t tm_dh, unsig
     tmem_wait_ld();
     uint32_t p[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e)
-      p[e] = pack_bf16x2(__uint_as_float(v[2 * e]) * bf16_lo(dh[e]),
-                         __uint_as_float(v[2 * e + 1]) * bf16_hi(dh[e]));
+    for (int e = 0; e < 16; ++e) {
+      const float2 g =
+          __fmul2_rn(make_float2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1])),
+                     make_float2(bf16_lo(dh[e]), bf16_hi(dh[e])));
+      p[e] = pack_bf16x2(g.x, g.y);
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
       *reinterpret_cast<uint4 *>(dst + canon_offset(r, c + 8 * e, 64)) =
@@ -258,7 +273,7 @@ __device__ __forceinline__ void park_row(uint32_t tm, unsigned char *g, int r) {
 // (h2 as stored), the output's term of the rho-derivative before its 1/rho.
 __device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *hdst,
                                                unsigned char *g, int r) {
-  float dot0 = 0.f, dot1 = 0.f;
+  float2 dot = make_float2(0.f, 0.f);  // even and odd units
 #pragma unroll
   for (int c = 0; c < HIDDEN; c += 32) {
     uint32_t v[32];
@@ -271,14 +286,14 @@ __device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *h
       uint32_t hp[4], ap[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float h0, h1, d0, d1;
-        tanh_and_slope(__uint_as_float(v[8 * e + 2 * q]), h0, d0);
-        tanh_and_slope(__uint_as_float(v[8 * e + 2 * q + 1]), h1, d1);
-        hp[q] = pack_bf16x2(h0, h1);
-        const float g0 = bf16_lo(gw[q]), g1 = bf16_hi(gw[q]);
-        ap[q] = pack_bf16x2(g0 * d0, g1 * d1);
-        dot0 = fmaf(g0, bf16_lo(hp[q]), dot0);
-        dot1 = fmaf(g1, bf16_hi(hp[q]), dot1);
+        float2 h, dh;
+        tanh_and_slope2(__uint_as_float(v[8 * e + 2 * q]), __uint_as_float(v[8 * e + 2 * q + 1]), h,
+                        dh);
+        hp[q] = pack_bf16x2(h.x, h.y);
+        const float2 g = make_float2(bf16_lo(gw[q]), bf16_hi(gw[q]));
+        const float2 a = __fmul2_rn(g, dh);
+        ap[q] = pack_bf16x2(a.x, a.y);
+        dot = __ffma2_rn(g, make_float2(bf16_lo(hp[q]), bf16_hi(hp[q])), dot);
       }
       *reinterpret_cast<uint4 *>(hdst + canon_offset(r, c + 8 * e, 64)) =
           make_uint4(hp[0], hp[1], hp[2], hp[3]);
@@ -286,7 +301,7 @@ __device__ __forceinline__ float tanh_grad_row(uint32_t tm_row, unsigned char *h
           make_uint4(ap[0], ap[1], ap[2], ap[3]);
     }
   }
-  return dot0 + dot1;
+  return dot.x + dot.y;
 }
 
 struct TilePos {
