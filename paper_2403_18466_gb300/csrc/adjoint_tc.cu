@@ -529,6 +529,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before_sync();     \
   named_barrier(bar_id, WG_THREADS);
 
+    float dn[Q], pbn[Q];  // the next tile's inputs
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      dn[i] = 0.f;
+      pbn[i] = 0.f;
+    }
     for (int it = 0; it < count; ++it) {
       // The previous tile's weight-gradient GEMMs may still be reading its
       // buffers: dW2 reads h1 and dL/da2 (waited for before this tile's
@@ -541,13 +547,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool active = x < nx;
       const int ym = T.y == 0 ? ny - 1 : T.y - 1, yp = T.y == ny - 1 ? 0 : T.y + 1;
       const int xm = x == 0 ? nx - 1 : x - 1, xp = x >= nx - 1 ? 0 : x + 1;
+      // this tile's populations and incoming adjoint: loaded during the
+      // previous tile's last GEMM, or here for the first tile
       float d[Q], pb[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        d[i] = 0.f;
-        pb[i] = 0.f;
+        d[i] = dn[i];
+        pb[i] = pbn[i];
       }
-      if (active) {
+      if (active && it == 0) {
         const float *gb = state + (size_t)T.b * Q * plane;
         const float *lb = lam_next + (size_t)T.b * Q * plane + T.y * nx + x;
 #pragma unroll
@@ -706,6 +714,31 @@ __global__ void __launch_bounds__(THREADS, 1)
                    smem_desc(s_w1t + 256 * s, 128, 1024), ID16, s > 0);
         mma_commit(bar);
         pending = true;
+      }
+      // ---- the next tile's inputs into registers while the last GEMM runs
+      // (they were prefetched into the L2 cache at this tile's start)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dn[i] = 0.f;
+        pbn[i] = 0.f;
+      }
+      if (it + 1 < count) {
+        TilePos N = T;
+        N.advance(nx, ny);
+        const int xn = N.x0 + r;
+        if (xn < nx) {
+          const int nym = N.y == 0 ? ny - 1 : N.y - 1, nyp = N.y == ny - 1 ? 0 : N.y + 1;
+          const int nxm = xn == 0 ? nx - 1 : xn - 1, nxp = xn >= nx - 1 ? 0 : xn + 1;
+          const float *gb = state + (size_t)N.b * Q * plane;
+          const float *lb = lam_next + (size_t)N.b * Q * plane + N.y * nx + xn;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const int xs = cx(i) == 0 ? xn : (cx(i) == 1 ? nxm : nxp);
+            const int ys = cy(i) == 0 ? N.y : (cy(i) == 1 ? nym : nyp);
+            dn[i] = __ldg(gb + (size_t)i * plane + ys * nx + xs);
+            pbn[i] = __ldg(lb + (size_t)i * plane);
+          }
+        }
       }
       WAIT_OWN_OR_BREAK()
       // ---- dL/dx -> rest of the chain rule (FP32), scatter lam to x - c_i
