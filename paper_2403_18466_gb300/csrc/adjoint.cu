@@ -11,7 +11,9 @@
 // recomputes the node's forward values (x, h1, h2, o), runs the chain rule
 // backwards per node, scatters lam, and stages the per-node vectors in shared
 // memory to accumulate the weight gradient as sums of outer products over the
-// tile.  Each CTA writes its own row of partial sums; a second kernel adds
+// tile.  The staging buffers hold one CTA per SM, so the per-node phase keeps
+// its vectors in registers (up to 255 per thread are free at 128 threads) and
+// reads the weights as float4 broadcasts.  Each CTA writes its own row of partial sums; a second kernel adds
 // the rows in a fixed order, so dtheta is bitwise reproducible.
 #include "kernels.h"
 #include "lattice.cuh"
@@ -22,6 +24,10 @@ namespace {
 constexpr int AT = 128;      // threads per CTA = nodes per tile
 constexpr int HP = 68;       // padded row stride of the staged hidden vectors
 constexpr int XP = 12;       // padded row stride of 9-vectors
+// hidden units per group of independent accumulators in the 64 x 64 products
+// (8 or 16 measured slower)
+constexpr int G2 = 4;
+static_assert(G2 % 4 == 0 && HIDDEN % G2 == 0, "accumulator groups");
 
 struct __align__(16) AdjSmem {
   float w1[HIDDEN][XP];      // [j][k]
@@ -118,36 +124,86 @@ __global__ void __launch_bounds__(AT, 1)
       shifted_feq(m, deq);
       const float inv_rho = 1.0f / m.rho;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        xin[i] = (d[i] - deq[i]) * inv_rho;
-        S.X[t][i] = xin[i];
+      for (int i = 0; i < Q; ++i) xin[i] = (d[i] - deq[i]) * inv_rho;
+      // Per-node vectors are written to (and read from) this thread's rows of
+      // the staging buffers with 16-byte accesses (a row stride of 68 floats
+      // keeps those free of bank conflicts); weights are read as float4
+      // broadcasts.
+      {
+        float4 *xr = reinterpret_cast<float4 *>(&S.X[t][0]);
+        xr[0] = make_float4(xin[0], xin[1], xin[2], xin[3]);
+        xr[1] = make_float4(xin[4], xin[5], xin[6], xin[7]);
+        xr[2] = make_float4(xin[8], 1.0f, 0.f, 0.f);
       }
-      S.X[t][9] = 1.0f;
-      for (int j = 0; j < HIDDEN; ++j) {
-        float a = S.b1[j];
+      float h1[HIDDEN];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a = fmaf(S.w1[j][k], xin[k], a);
-        S.H1[t][j] = tanhf(a);
+      for (int j = 0; j < HIDDEN; ++j) {
+        const float4 wa = *reinterpret_cast<const float4 *>(&S.w1[j][0]);
+        const float4 wb = *reinterpret_cast<const float4 *>(&S.w1[j][4]);
+        float a = S.b1[j];
+        a = fmaf(wa.x, xin[0], a);
+        a = fmaf(wa.y, xin[1], a);
+        a = fmaf(wa.z, xin[2], a);
+        a = fmaf(wa.w, xin[3], a);
+        a = fmaf(wb.x, xin[4], a);
+        a = fmaf(wb.y, xin[5], a);
+        a = fmaf(wb.z, xin[6], a);
+        a = fmaf(wb.w, xin[7], a);
+        a = fmaf(S.w1[j][8], xin[8], a);
+        h1[j] = tanhf(a);
+      }
+      {
+        float4 *hr = reinterpret_cast<float4 *>(&S.H1[t][0]);
+#pragma unroll
+        for (int q = 0; q < HIDDEN / 4; ++q)
+          hr[q] = make_float4(h1[4 * q], h1[4 * q + 1], h1[4 * q + 2], h1[4 * q + 3]);
       }
       float o[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) o[i] = S.b3[i];
-      for (int j = 0; j < HIDDEN; j += 4) {
-        float a0 = S.b2[j], a1 = S.b2[j + 1], a2 = S.b2[j + 2], a3 = S.b2[j + 3];
-#pragma unroll 8
-        for (int k = 0; k < HIDDEN; ++k) {
-          const float h = S.H1[t][k];
-          a0 = fmaf(S.w2[j][k], h, a0);
-          a1 = fmaf(S.w2[j + 1][k], h, a1);
-          a2 = fmaf(S.w2[j + 2][k], h, a2);
-          a3 = fmaf(S.w2[j + 3][k], h, a3);
+      for (int j = 0; j < HIDDEN; j += G2) {
+        float acc[G2];
+        const float4 *rw[G2];
+#pragma unroll
+        for (int g = 0; g < G2; ++g) {
+          acc[g] = S.b2[j + g];
+          rw[g] = reinterpret_cast<const float4 *>(&S.w2[j + g][0]);
         }
-        const float hv[4] = {tanhf(a0), tanhf(a1), tanhf(a2), tanhf(a3)};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          S.H2[t][j + q] = hv[q];
+        for (int k4 = 0; k4 < HIDDEN / 4; ++k4) {
+          float4 u[G2];
 #pragma unroll
-          for (int i = 0; i < Q; ++i) o[i] = fmaf(S.w3t[j + q][i], hv[q], o[i]);
+          for (int g = 0; g < G2; ++g) u[g] = rw[g][k4];
+          const float *h = &h1[4 * k4];
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].x, h[0], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].y, h[1], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].z, h[2], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].w, h[3], acc[g]);
+        }
+        float hv[G2];
+#pragma unroll
+        for (int g = 0; g < G2; ++g) hv[g] = tanhf(acc[g]);
+#pragma unroll
+        for (int g = 0; g < G2; g += 4)
+          *reinterpret_cast<float4 *>(&S.H2[t][j + g]) =
+              make_float4(hv[g], hv[g + 1], hv[g + 2], hv[g + 3]);
+#pragma unroll
+        for (int q = 0; q < G2; ++q) {
+          const float4 c0 = *reinterpret_cast<const float4 *>(&S.w3t[j + q][0]);
+          const float4 c1 = *reinterpret_cast<const float4 *>(&S.w3t[j + q][4]);
+          o[0] = fmaf(c0.x, hv[q], o[0]);
+          o[1] = fmaf(c0.y, hv[q], o[1]);
+          o[2] = fmaf(c0.z, hv[q], o[2]);
+          o[3] = fmaf(c0.w, hv[q], o[3]);
+          o[4] = fmaf(c1.x, hv[q], o[4]);
+          o[5] = fmaf(c1.y, hv[q], o[5]);
+          o[6] = fmaf(c1.z, hv[q], o[6]);
+          o[7] = fmaf(c1.w, hv[q], o[7]);
+          o[8] = fmaf(S.w3t[j + q][8], hv[q], o[8]);
         }
       }
       S.H2[t][HIDDEN] = 1.0f;
@@ -179,42 +235,93 @@ __global__ void __launch_bounds__(AT, 1)
         }
       }
       project9(ohb);  // dL/do = P^T dL/dohat, P symmetric
-#pragma unroll
-      for (int i = 0; i < Q; ++i) S.OB[t][i] = ohb[i];
-      // dL/da2 = (W3^T dL/do) * (1 - h2^2)
-      for (int j = 0; j < HIDDEN; ++j) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) s = fmaf(S.w3t[j][i], ohb[i], s);
-        const float h = S.H2[t][j];
-        S.A2[t][j] = s * (1.0f - h * h);
+      {
+        float4 *orow = reinterpret_cast<float4 *>(&S.OB[t][0]);
+        orow[0] = make_float4(ohb[0], ohb[1], ohb[2], ohb[3]);
+        orow[1] = make_float4(ohb[4], ohb[5], ohb[6], ohb[7]);
+        orow[2] = make_float4(ohb[8], 0.f, 0.f, 0.f);
       }
-      // dL/da1 = (W2^T dL/da2) * (1 - h1^2)
-      for (int k = 0; k < HIDDEN; k += 4) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < HIDDEN; ++j) {
-          const float a = S.A2[t][j];
-          s0 = fmaf(S.w2t[k][j], a, s0);
-          s1 = fmaf(S.w2t[k + 1][j], a, s1);
-          s2 = fmaf(S.w2t[k + 2][j], a, s2);
-          s3 = fmaf(S.w2t[k + 3][j], a, s3);
-        }
-        const float sv[4] = {s0, s1, s2, s3};
+      // dL/da2 = (W3^T dL/do) * (1 - h2^2), kept in registers
+      float a2v[HIDDEN];
+#pragma unroll
+      for (int j4 = 0; j4 < HIDDEN / 4; ++j4) {
+        const float4 h4 = *reinterpret_cast<const float4 *>(&S.H2[t][4 * j4]);
+        const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float h = S.H1[t][k + q];
-          S.A1[t][k + q] = sv[q] * (1.0f - h * h);
+          const int j = 4 * j4 + q;
+          const float4 c0 = *reinterpret_cast<const float4 *>(&S.w3t[j][0]);
+          const float4 c1 = *reinterpret_cast<const float4 *>(&S.w3t[j][4]);
+          float s = 0.f;
+          s = fmaf(c0.x, ohb[0], s);
+          s = fmaf(c0.y, ohb[1], s);
+          s = fmaf(c0.z, ohb[2], s);
+          s = fmaf(c0.w, ohb[3], s);
+          s = fmaf(c1.x, ohb[4], s);
+          s = fmaf(c1.y, ohb[5], s);
+          s = fmaf(c1.z, ohb[6], s);
+          s = fmaf(c1.w, ohb[7], s);
+          s = fmaf(S.w3t[j][8], ohb[8], s);
+          const float h = hh[q];
+          a2v[j] = s * (1.0f - h * h);
         }
+        *reinterpret_cast<float4 *>(&S.A2[t][4 * j4]) =
+            make_float4(a2v[4 * j4], a2v[4 * j4 + 1], a2v[4 * j4 + 2], a2v[4 * j4 + 3]);
       }
-      // dL/dx = W1^T dL/da1
+      // dL/da1 = (W2^T dL/da2) * (1 - h1^2), and dL/dx = W1^T dL/da1
       float xb[Q];
 #pragma unroll
       for (int k = 0; k < Q; ++k) xb[k] = 0.f;
-      for (int j = 0; j < HIDDEN; ++j) {
-        const float a = S.A1[t][j];
+      for (int k = 0; k < HIDDEN; k += G2) {
+        float acc[G2];
+        const float4 *rw[G2];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) xb[k] = fmaf(S.w1[j][k], a, xb[k]);
+        for (int g = 0; g < G2; ++g) {
+          acc[g] = 0.f;
+          rw[g] = reinterpret_cast<const float4 *>(&S.w2t[k + g][0]);
+        }
+#pragma unroll
+        for (int j4 = 0; j4 < HIDDEN / 4; ++j4) {
+          float4 u[G2];
+#pragma unroll
+          for (int g = 0; g < G2; ++g) u[g] = rw[g][j4];
+          const float *a = &a2v[4 * j4];
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].x, a[0], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].y, a[1], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].z, a[2], acc[g]);
+#pragma unroll
+          for (int g = 0; g < G2; ++g) acc[g] = fmaf(u[g].w, a[3], acc[g]);
+        }
+        float av[G2];
+#pragma unroll
+        for (int g = 0; g < G2; g += 4) {
+          const float4 h4 = *reinterpret_cast<const float4 *>(&S.H1[t][k + g]);
+          const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float h = hh[q];
+            av[g + q] = acc[g + q] * (1.0f - h * h);
+          }
+          *reinterpret_cast<float4 *>(&S.A1[t][k + g]) =
+              make_float4(av[g], av[g + 1], av[g + 2], av[g + 3]);
+        }
+#pragma unroll
+        for (int q = 0; q < G2; ++q) {
+          const float4 wa = *reinterpret_cast<const float4 *>(&S.w1[k + q][0]);
+          const float4 wb = *reinterpret_cast<const float4 *>(&S.w1[k + q][4]);
+          xb[0] = fmaf(wa.x, av[q], xb[0]);
+          xb[1] = fmaf(wa.y, av[q], xb[1]);
+          xb[2] = fmaf(wa.z, av[q], xb[2]);
+          xb[3] = fmaf(wa.w, av[q], xb[3]);
+          xb[4] = fmaf(wb.x, av[q], xb[4]);
+          xb[5] = fmaf(wb.y, av[q], xb[5]);
+          xb[6] = fmaf(wb.z, av[q], xb[6]);
+          xb[7] = fmaf(wb.w, av[q], xb[7]);
+          xb[8] = fmaf(S.w1[k + q][8], av[q], xb[8]);
+        }
       }
       // x = (f - feq) / rho
 #pragma unroll
@@ -299,19 +406,40 @@ __global__ void __launch_bounds__(AT, 1)
       }
     }
     {
-      // [dW3 | db3][i][j] += sum_n OB[n][i] [h2 | 1][n][j]: 9 x 65 entries
-      for (int e = t; e < 9 * (HIDDEN + 1); e += AT) {
-        const int i = e / (HIDDEN + 1), j = e % (HIDDEN + 1);
-        float c = 0.f;
-        for (int n = 0; n < AT; ++n) c = fmaf(S.OB[n][i], S.H2[n][j], c);
-        if (j < HIDDEN) S.acc[OFF_W3 + i * HIDDEN + j] += c;
-        else S.acc[OFF_B3 + i] += c;
-      }
-      // db2[j] += sum_n A2[n][j]
-      if (t < HIDDEN) {
-        float c = 0.f;
-        for (int n = 0; n < AT; ++n) c += S.A2[n][t];
-        S.acc[OFF_B2 + t] += c;
+      // [dW3 | db3][i][j] += sum_n OB[n][i] [h2 | 1][n][j]: 9 x 65 entries,
+      // thread j < 65 owning column j (dL/do rows read as float4 broadcasts)
+      if (t <= HIDDEN) {
+        const int j = t;
+        float c[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) c[i] = 0.f;
+        for (int n = 0; n < AT; ++n) {
+          const float4 o0 = *reinterpret_cast<const float4 *>(&S.OB[n][0]);
+          const float4 o1 = *reinterpret_cast<const float4 *>(&S.OB[n][4]);
+          const float o8 = S.OB[n][8];
+          const float h = S.H2[n][j];
+          c[0] = fmaf(o0.x, h, c[0]);
+          c[1] = fmaf(o0.y, h, c[1]);
+          c[2] = fmaf(o0.z, h, c[2]);
+          c[3] = fmaf(o0.w, h, c[3]);
+          c[4] = fmaf(o1.x, h, c[4]);
+          c[5] = fmaf(o1.y, h, c[5]);
+          c[6] = fmaf(o1.z, h, c[6]);
+          c[7] = fmaf(o1.w, h, c[7]);
+          c[8] = fmaf(o8, h, c[8]);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (j < HIDDEN) S.acc[OFF_W3 + i * HIDDEN + j] += c[i];
+          else S.acc[OFF_B3 + i] += c[i];
+        }
+      } else {
+        // db2[j] += sum_n A2[n][j] on the remaining threads
+        for (int j = t - (HIDDEN + 1); j < HIDDEN; j += AT - (HIDDEN + 1)) {
+          float c = 0.f;
+          for (int n = 0; n < AT; ++n) c += S.A2[n][j];
+          S.acc[OFF_B2 + j] += c;
+        }
       }
     }
     __syncthreads();
