@@ -351,6 +351,12 @@ def run_gpu(args):
                "derivation": f"64 hidden-unit pairs per node, {xu8} of 8 on the XU at "
                              f"{XU_PAIR_CYCLES} sub-partition cycles per warp-wide pair "
                              "(measured), 4 sub-partitions per SM, measured SM clock"}
+    # the other bound next to the XU: instruction issue (ALU, FMA, XU, memory
+    # and tensor-memory instructions all take issue slots)
+    issue = _issue_bound(MLP_BF16_SOURCES, "k_step_mlp_bf16_2048.md", sms, sm_mhz)
+    if issue:
+        issue["frac"] = round(node_rate / issue["peak"], 4)
+    binding["issue"] = issue
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4),
                 "traffic": _traffic_from_profile(MLP_BF16_SOURCES, "k_step_mlp_bf16_2048.md", nodes),
@@ -763,9 +769,9 @@ def kernel_code_digest(kernel_sources):
     return h.hexdigest()
 
 
-def _traffic_from_profile(kernel_sources, summary, nodes):
-    """DRAM bytes per launch of the step kernel from a committed ncu summary,
-    scaled to `nodes`; None if the kernel code changed since the capture."""
+def _profile_fields(kernel_sources, summary):
+    """The "- key: value" fields of a committed ncu summary, or None if the
+    kernel code changed since the capture (or the summary is unreadable)."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         fields = {}
@@ -775,9 +781,35 @@ def _traffic_from_profile(kernel_sources, summary, nodes):
                 fields[k.strip()] = v.strip().strip("`")
         if fields.get("code_sha256") != kernel_code_digest(kernel_sources):
             return None
-        return float(fields["dram_bytes_per_launch"]) * nodes / float(fields["nodes_per_launch"])
+        return fields
     except Exception:
         return None
+
+
+def _traffic_from_profile(kernel_sources, summary, nodes):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    scaled to `nodes`; None if the kernel code changed since the capture."""
+    f = _profile_fields(kernel_sources, summary)
+    try:
+        return float(f["dram_bytes_per_launch"]) * nodes / float(f["nodes_per_launch"])
+    except Exception:
+        return None
+
+
+def _issue_bound(kernel_sources, summary, sms, sm_mhz):
+    """Instruction-issue bound of the step kernel: its warp instructions per
+    node (committed ncu summary; None once the kernel code has changed) at four
+    warp instructions per SM cycle (one per sub-partition), in MLUPS."""
+    f = _profile_fields(kernel_sources, summary)
+    try:
+        per_node = float(f["warp_instructions_per_launch"]) / float(f["nodes_per_launch"])
+    except Exception:
+        return None
+    cycles = per_node / 4.0
+    return {"peak": round(sms * sm_mhz / cycles, 1), "peak_unit": "MLUPS",
+            "warp_instructions_per_node": round(per_node, 2),
+            "sm_cycles_per_node": round(cycles, 3),
+            "source": f"profiles/{summary} (smsp__inst_executed.sum of one launch)"}
 
 
 def main():
