@@ -446,6 +446,13 @@ def _time_training(lbm, torch, dev, inputs):
     for prec in ("f32", "bf16"):
         res = {}
         for rep in range(3):
+            # the same 16 steps without a record (the inference forward)
+            lat.set_state(f0)
+            ev[0].record()
+            lat.step(L, "mlp_f32" if prec == "f32" else "mlp_bf16", w)
+            ev[1].record()
+            ev[1].synchronize()
+            plain_ms = ev[0].elapsed_time(ev[1])
             lat.set_state(f0)
             ev[0].record()
             lat.forward_record(L, ck, w, ws, prec)
@@ -454,11 +461,14 @@ def _time_training(lbm, torch, dev, inputs):
             lat.backward(g, w, ws, dW, None, prec)
             ev[2].record()
             ev[2].synchronize()
-            res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2])}
+            res = {"fwd_ms": ev[0].elapsed_time(ev[1]), "fwd_adj_ms": ev[0].elapsed_time(ev[2]),
+                   "plain_ms": plain_ms}
         out[prec] = {"fwd_ms_per_step": round(res["fwd_ms"] / L, 4),
                      "fwd_adj_ms_per_step": round(res["fwd_adj_ms"] / L, 4),
                      "ratio_fwd_adj_over_fwd": round(res["fwd_adj_ms"] / res["fwd_ms"], 3),
-                     "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1)}
+                     "fwd_mlups": round(nodes * L / (res["fwd_ms"] * 1e-3) / 1e6, 1),
+                     "plain_fwd_ms_per_step": round(res["plain_ms"] / L, 4),
+                     "ratio_fwd_adj_over_plain_fwd": round(res["fwd_adj_ms"] / res["plain_ms"], 3)}
     out["ratio_bf16_fwd_adj_over_f32_fwd"] = round(
         out["bf16"]["fwd_adj_ms_per_step"] / out["f32"]["fwd_ms_per_step"], 3)
     # the memory / recompute trade of the checkpoint interval k (tensor-core

@@ -358,15 +358,21 @@ static int forward_record(lbm_ctx *c, lbm_collision kind, int n, int k, const lb
   if (ws_bytes < lbm_record_bytes(&c->p, n, k)) return LBM_ERR_ARG;
   const size_t sb = state_bytes(&c->p);
   char *base = static_cast<char *>(ws);
+  // Checkpoint 0 is a copy of the current state.  Every later checkpoint
+  // g^{jk} (jk < n) is written there by the step that produces it, and the
+  // next step reads it from there, so the record costs one copy, not n/k;
+  // the steps in between alternate between the two state buffers, and the
+  // last one (g^n is never a checkpoint) ends in a state buffer.
+  CUDA_TRY(cudaMemcpyAsync(base, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
+  const float *in = c->buf[c->cur];
   for (int s = 0; s < n; ++s) {
-    if (s % k == 0)
-      CUDA_TRY(cudaMemcpyAsync(base + (size_t)(s / k) * sb, c->buf[c->cur], sb,
-                               cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(one_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], kind, w, s % k != 0));
-    c->cur ^= 1;
+    const bool to_ck = (s + 1) % k == 0 && s + 1 < n;
+    float *out = to_ck ? reinterpret_cast<float *>(base + (size_t)((s + 1) / k) * sb)
+                       : c->buf[c->cur ^ 1];
+    CUDA_TRY(one_step(c, in, out, kind, w, s > 0));
+    if (!to_ck) c->cur ^= 1;
+    in = out;
   }
-  if (n == 0)
-    CUDA_TRY(cudaMemcpyAsync(base, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
   c->rec_n = n;
   c->rec_k = k;
   c->rec_ws = ws;

@@ -135,3 +135,43 @@ def test_tensor_core_backward_matches_oracle(lbm, nx, ny, B, steps, ck, record):
     dW2 = torch.empty_like(dW)
     lat.backward(dL_df, w, ws, dW2, None, "bf16")
     assert torch.equal(dW, dW2)
+
+
+@pytest.mark.parametrize("pair", ["f32", "bf16"])
+def test_checkpoint_interval_changes_no_bits(lbm, pair):
+    """The record copies the start state once and has every later checkpoint
+    written by the step that produces it; the backward recomputes each segment
+    from its checkpoint with the same kernel.  Every state the adjoint sees is
+    therefore the same bits for any interval k, and so are the final state,
+    the loss, dtheta and dL/df0 (n = 5: k = 2 and 3 leave a ragged last
+    segment, k = 5 records only the start)."""
+    nx, ny, B, n = 200, 24, 2, 5
+    theta = inputs.xavier_mlp(7, bias_scale=0.3, gain=3.0, out_scale=0.01)
+    f0 = _dev(population_field(B, ny, nx, seed=91, neq=0.05))
+    utx = _dev(inputs.noise((B, ny, nx), 92, 0.03))
+    uty = _dev(inputs.noise((B, ny, nx), 93, 0.03))
+    kind = "mlp_f32" if pair == "f32" else "mlp_bf16"
+    lat = lbm.Lattice(nx, ny, B, tau=0.6, force_amp=1e-4, force_mode=1, device=DEV)
+    w = lbm.weights_struct(_dev(theta))
+    lat.set_state(f0)
+    lat.step(n, kind, w)
+    plain = lat.get_state()
+    runs = {}
+    for k in (1, 2, 3, 5):
+        lat.set_state(f0)
+        ws = torch.empty(lat.record_bytes(n, k) // 4, dtype=torch.float32, device=DEV)
+        lat.forward_record(n, k, w, ws, pair)
+        fin = lat.get_state()
+        loss, dL_df = lat.velocity_loss(utx, uty)
+        dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=DEV)
+        dF0 = torch.empty_like(dL_df)
+        lat.backward(dL_df, w, ws, dW, dF0, pair)
+        assert lat.status() == lbm.LBM_OK
+        # the context's state is the recorded run's end, untouched by the backward
+        assert torch.equal(lat.get_state(), fin)
+        runs[k] = (fin, loss.clone(), dW, dF0)
+    assert torch.equal(runs[1][0], plain)
+    assert float(runs[1][2].abs().max()) > 0
+    for k in (2, 3, 5):
+        for a, b in zip(runs[1], runs[k]):
+            assert torch.equal(a, b), f"k = {k}"
