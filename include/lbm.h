@@ -253,7 +253,9 @@ int lbm_backward(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights *w, v
  * rounding of activations and adjoints: a few per cent relative L2 of dtheta
  * for a velocity loss (whose weight-gradient sums over nodes cancel strongly),
  * against 1e-4 for the FP32 adjoint.  Same arguments and conventions as the
- * FP32 pair. */
+ * FP32 pair; lbm_backward_bf16 takes lattices of fewer than 2^31 / 9
+ * population values in all (nx * ny * batch < 238,609,295) and returns
+ * LBM_ERR_ARG beyond that. */
 int lbm_forward_record_bf16(lbm_ctx *ctx, int n, int ckpt_every, const lbm_weights *w, void *ws,
                             size_t ws_bytes);
 int lbm_backward_bf16(lbm_ctx *ctx, const float *dL_df_final, const lbm_weights *w, void *ws,

@@ -395,6 +395,8 @@ static int backward(lbm_ctx *c, bool tc, const float *dL_df_final, const lbm_wei
   if (!c || !dL_df_final || !ws || !dW) return LBM_ERR_ARG;
   if (!w || check_weights(LBM_MLP_F32, w) != LBM_OK) return LBM_ERR_ARG;
   if (ws != c->rec_ws) return LBM_ERR_ARG;  // needs the workspace of the last record
+  // the tensor-core adjoint's launcher takes fewer than 2^31 population values
+  if (tc && (long long)c->g.nodes() * 9 >= (1LL << 31)) return LBM_ERR_ARG;
   // segments are recomputed with the collision the record used
   const lbm_collision kind = c->rec_kind;
   const int n = c->rec_n, k = c->rec_k;
