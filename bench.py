@@ -472,10 +472,11 @@ def _time_training(lbm, torch, dev, inputs):
     out["ratio_bf16_fwd_adj_over_f32_fwd"] = round(
         out["bf16"]["fwd_adj_ms_per_step"] / out["f32"]["fwd_ms_per_step"], 3)
     # the memory / recompute trade of the checkpoint interval k (tensor-core
-    # pair, same 16-step unroll): the backward recomputes (k - 1)/k of a
-    # forward step per step and the workspace holds ceil(16/k) + k + 1 states
+    # pair, same 16-step unroll): the backward recomputes the k - 1 inner
+    # states of every segment but the last (which the record keeps) and the
+    # workspace holds ceil(16/k) + k + 1 states
     sweep = {}
-    for ck_i in (1, 2, 4, 8):
+    for ck_i in (1, 2, 4, 8, 16):
         ws_i = torch.empty(lat.record_bytes(L, ck_i) // 4, dtype=torch.float32, device=dev)
         for rep in range(3):
             lat.set_state(f0)

@@ -224,7 +224,9 @@ size_t lbm_record_bytes(const lbm_params *p, int n, int ckpt_every);
 /* Unrolled training forward (SI section 2): advance n steps with the FP32
  * learned collision, storing the state every ckpt_every steps into `ws`
  * (device, >= lbm_record_bytes).  The start state is copied into `ws`; each
- * later checkpoint is written there by the step that produces it (no copy).
+ * later checkpoint is written there by the step that produces it (no copy),
+ * and the states inside the last segment are kept in the workspace's
+ * recompute area, so the backward recomputes only the earlier segments.
  * The context ends at step n, as after lbm_step(n, LBM_MLP_F32). */
 int lbm_forward_record(lbm_ctx *ctx, int n, int ckpt_every, const lbm_weights *w, void *ws,
                        size_t ws_bytes);

@@ -42,6 +42,7 @@ struct lbm_ctx {
   int rec_n, rec_k;
   const void *rec_ws;
   lbm_collision rec_kind;
+  bool rec_last_seg;  // the recompute area of rec_ws holds the last segment's states
 };
 
 namespace {
@@ -360,23 +361,37 @@ static int forward_record(lbm_ctx *c, lbm_collision kind, int n, int k, const lb
   char *base = static_cast<char *>(ws);
   // Checkpoint 0 is a copy of the current state.  Every later checkpoint
   // g^{jk} (jk < n) is written there by the step that produces it, and the
-  // next step reads it from there, so the record costs one copy, not n/k;
-  // the steps in between alternate between the two state buffers, and the
-  // last one (g^n is never a checkpoint) ends in a state buffer.
+  // next step reads it from there, so the record costs one copy, not n/k.
+  // The states inside the last segment, g^{s0+1} .. g^{n-1}, go where the
+  // backward would recompute them (the workspace's k - 1 recompute states),
+  // so the backward starts without a recompute.  The other steps alternate
+  // between the two state buffers, and the last one (g^n is never stored in
+  // the workspace) ends in a state buffer.
+  const int last_s0 = n > 0 ? ((n - 1) / k) * k : 0;
+  float *seg = reinterpret_cast<float *>(base + (size_t)n_checkpoints(n, k) * sb);
+  const size_t sf = sb / sizeof(float);
+  c->rec_last_seg = false;
   CUDA_TRY(cudaMemcpyAsync(base, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
   const float *in = c->buf[c->cur];
   for (int s = 0; s < n; ++s) {
-    const bool to_ck = (s + 1) % k == 0 && s + 1 < n;
-    float *out = to_ck ? reinterpret_cast<float *>(base + (size_t)((s + 1) / k) * sb)
-                       : c->buf[c->cur ^ 1];
+    const int t = s + 1;  // the state this step produces
+    float *out;
+    bool to_buf = false;
+    if (t % k == 0 && t < n)
+      out = reinterpret_cast<float *>(base + (size_t)(t / k) * sb);
+    else if (t > last_s0 && t < n)
+      out = seg + (size_t)(t - last_s0 - 1) * sf;
+    else
+      out = c->buf[c->cur ^ 1], to_buf = true;
     CUDA_TRY(one_step(c, in, out, kind, w, s > 0));
-    if (!to_ck) c->cur ^= 1;
+    if (to_buf) c->cur ^= 1;
     in = out;
   }
   c->rec_n = n;
   c->rec_k = k;
   c->rec_ws = ws;
   c->rec_kind = kind;
+  c->rec_last_seg = n > 0;
   return LBM_OK;
 }
 
@@ -416,13 +431,19 @@ static int backward(lbm_ctx *c, bool tc, const float *dL_df_final, const lbm_wei
   CUDA_TRY(lbm::launch_push(c->g, dL_df_final, lam[0], c->stream));
   int cur = 0;
   bool first = true;
-  for (int s0 = ((n - 1) / k) * k; n > 0 && s0 >= 0; s0 -= k) {
+  const int last_s0 = n > 0 ? ((n - 1) / k) * k : 0;
+  for (int s0 = last_s0; n > 0 && s0 >= 0; s0 -= k) {
     const float *ck = reinterpret_cast<const float *>(base + (size_t)(s0 / k) * sb);
     const int len = (s0 + k <= n) ? k : n - s0;
-    // recompute g^{s0+1} .. g^{s0+len-1} into seg[0 .. len-2]
-    for (int j = 1; j < len; ++j) {
-      const float *in = j == 1 ? ck : seg + (size_t)(j - 2) * sf;
-      CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, kind, w, j > 1));
+    // g^{s0+1} .. g^{s0+len-1} in seg[0 .. len-2]: left there by the record
+    // for the last segment (until a recompute of another segment overwrites
+    // them), recomputed from the checkpoint otherwise
+    if (!(s0 == last_s0 && c->rec_last_seg) && len > 1) {
+      for (int j = 1; j < len; ++j) {
+        const float *in = j == 1 ? ck : seg + (size_t)(j - 2) * sf;
+        CUDA_TRY(one_step(c, in, seg + (size_t)(j - 1) * sf, kind, w, j > 1));
+      }
+      c->rec_last_seg = s0 == last_s0;
     }
     for (int j = len - 1; j >= 0; --j) {
       const float *gs = j == 0 ? ck : seg + (size_t)(j - 1) * sf;

@@ -139,12 +139,15 @@ def test_tensor_core_backward_matches_oracle(lbm, nx, ny, B, steps, ck, record):
 
 @pytest.mark.parametrize("pair", ["f32", "bf16"])
 def test_checkpoint_interval_changes_no_bits(lbm, pair):
-    """The record copies the start state once and has every later checkpoint
-    written by the step that produces it; the backward recomputes each segment
-    from its checkpoint with the same kernel.  Every state the adjoint sees is
-    therefore the same bits for any interval k, and so are the final state,
-    the loss, dtheta and dL/df0 (n = 5: k = 2 and 3 leave a ragged last
-    segment, k = 5 records only the start)."""
+    """The record copies the start state once, has every later checkpoint
+    written by the step that produces it and keeps the last segment's states
+    where the backward would recompute them; the backward recomputes the other
+    segments from their checkpoints with the same kernel.  Every state the
+    adjoint sees is therefore the same bits for any interval k, and so are the
+    final state, the loss, dtheta and dL/df0 (n = 5: k = 2 and 3 leave a
+    ragged last segment, k = 5 records only the start).  A second backward
+    (whose last segment, for k = 3, has been overwritten by the first one's
+    recompute of the other segment) gives the same bits again."""
     nx, ny, B, n = 200, 24, 2, 5
     theta = inputs.xavier_mlp(7, bias_scale=0.3, gain=3.0, out_scale=0.01)
     f0 = _dev(population_field(B, ny, nx, seed=91, neq=0.05))
@@ -166,7 +169,10 @@ def test_checkpoint_interval_changes_no_bits(lbm, pair):
         dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=DEV)
         dF0 = torch.empty_like(dL_df)
         lat.backward(dL_df, w, ws, dW, dF0, pair)
+        dW2, dF02 = torch.empty_like(dW), torch.empty_like(dF0)
+        lat.backward(dL_df, w, ws, dW2, dF02, pair)
         assert lat.status() == lbm.LBM_OK
+        assert torch.equal(dW, dW2) and torch.equal(dF0, dF02), f"k = {k}, second backward"
         # the context's state is the recorded run's end, untouched by the backward
         assert torch.equal(lat.get_state(), fin)
         runs[k] = (fin, loss.clone(), dW, dF0)
