@@ -732,9 +732,10 @@ def run_profile_case(args):
         if rc != lbm.LBM_OK:
             sys.exit(1)
         return
-    if args.profile == "adjoint_bf16":
-        # one unrolled training step of the tensor-core pair: 32 trajectories
-        # of --grid^2, --steps LES steps, checkpoint every 4
+    if args.profile in ("adjoint_bf16", "adjoint_f32"):
+        # one unrolled training step of the tensor-core (or FP32) pair: 32
+        # trajectories of --grid^2, --steps LES steps, checkpoint every 4
+        prec = args.profile.split("_")[1]
         B, n, L = 32, args.grid, args.steps
         lat = lbm.Lattice(n, n, B, tau=0.500375, force_amp=8e-5, force_mode=4, device=dev)
         ux = torch.tensor(inputs.noise((B, n, n), 5, 0.02), dtype=torch.float32, device=dev)
@@ -745,12 +746,12 @@ def run_profile_case(args):
         w = lbm.weights_struct(theta)
         ws = torch.empty(lat.record_bytes(L, 4) // 4, dtype=torch.float32, device=dev)
         dW = torch.empty(lbm.LBM_MLP_NPARAMS, dtype=torch.float32, device=dev)
-        lat.forward_record(L, 4, w, ws, "bf16")
+        lat.forward_record(L, 4, w, ws, prec)
         _, g = lat.velocity_loss(ux, uy)
-        lat.backward(g, w, ws, dW, None, "bf16")
+        lat.backward(g, w, ws, dW, None, prec)
         torch.cuda.synchronize()
         rc = lat.status()
-        print(f"profile case adjoint_bf16 32 x {n}^2 x {L}: {lbm.lbm_strerror(rc)}")
+        print(f"profile case {args.profile} 32 x {n}^2 x {L}: {lbm.lbm_strerror(rc)}")
         if rc != lbm.LBM_OK:
             sys.exit(1)
         return
@@ -832,7 +833,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default=None,
                     choices=["bgk", "smag", "mlp_bf16", "mlp_f32", "d3_bgk", "d3_smag",
-                             "d3_mlp_bf16", "d3_mlp_f32", "adjoint_bf16"],
+                             "d3_mlp_bf16", "d3_mlp_f32", "adjoint_bf16", "adjoint_f32"],
                     help="run a small case of one kernel for ncu and exit")
     ap.add_argument("--grid", type=int, default=2048)
     args = ap.parse_args()
