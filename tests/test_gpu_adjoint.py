@@ -145,7 +145,7 @@ def test_checkpoint_interval_changes_no_bits(lbm, pair):
     segments from their checkpoints with the same kernel.  Every state the
     adjoint sees is therefore the same bits for any interval k, and so are the
     final state, the loss, dtheta and dL/df0 (n = 5: k = 2 and 3 leave a
-    ragged last segment, k = 5 records only the start).  A second backward
+    ragged last segment, k = 5 and 8 record only the start).  A second backward
     (whose last segment, for k = 3, has been overwritten by the first one's
     recompute of the other segment) gives the same bits again."""
     nx, ny, B, n = 200, 24, 2, 5
@@ -160,7 +160,7 @@ def test_checkpoint_interval_changes_no_bits(lbm, pair):
     lat.step(n, kind, w)
     plain = lat.get_state()
     runs = {}
-    for k in (1, 2, 3, 5):
+    for k in (1, 2, 3, 5, 8):
         lat.set_state(f0)
         ws = torch.empty(lat.record_bytes(n, k) // 4, dtype=torch.float32, device=DEV)
         lat.forward_record(n, k, w, ws, pair)
@@ -178,6 +178,31 @@ def test_checkpoint_interval_changes_no_bits(lbm, pair):
         runs[k] = (fin, loss.clone(), dW, dF0)
     assert torch.equal(runs[1][0], plain)
     assert float(runs[1][2].abs().max()) > 0
-    for k in (2, 3, 5):
+    for k in (2, 3, 5, 8):
         for a, b in zip(runs[1], runs[k]):
             assert torch.equal(a, b), f"k = {k}"
+
+
+@pytest.mark.parametrize("pair", ["f32", "bf16"])
+def test_zero_step_record(lbm, pair):
+    """An unroll of n = 0 steps: the state is unchanged, dtheta is zero, and
+    dL/df0 is dL/df_final (the push of the final adjoint and the pull back
+    are inverse permutations, so the bits are kept)."""
+    nx, ny, B = 96, 10, 2
+    theta = inputs.xavier_mlp(7, bias_scale=0.3, gain=3.0, out_scale=0.01)
+    f0 = _dev(population_field(B, ny, nx, seed=95, neq=0.05))
+    lat = lbm.Lattice(nx, ny, B, tau=0.6, force_amp=1e-4, force_mode=1, device=DEV)
+    w = lbm.weights_struct(_dev(theta))
+    lat.set_state(f0)
+    before = lat.get_state()
+    ws = torch.empty(lat.record_bytes(0, 4) // 4, dtype=torch.float32, device=DEV)
+    lat.forward_record(0, 4, w, ws, pair)
+    loss, dL_df = lat.velocity_loss(_dev(inputs.noise((B, ny, nx), 96, 0.03)),
+                                    _dev(inputs.noise((B, ny, nx), 97, 0.03)))
+    dW = torch.full((lbm.LBM_MLP_NPARAMS,), float("nan"), dtype=torch.float32, device=DEV)
+    dF0 = torch.empty_like(dL_df)
+    lat.backward(dL_df, w, ws, dW, dF0, pair)
+    assert lat.status() == lbm.LBM_OK
+    assert torch.equal(lat.get_state(), before)
+    assert torch.equal(dW, torch.zeros_like(dW))
+    assert torch.equal(dF0, dL_df)
