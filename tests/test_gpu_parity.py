@@ -184,19 +184,22 @@ def test_unstable_state_sets_status(lbm):
     assert lat.status() == lbm.LBM_OK
 
 
-def test_run_host_matches_device_path(lbm):
-    B, ny, nx = 1, 40, 64
+@pytest.mark.parametrize("kind", ["mlp_f32", "mlp_bf16", "bgk"])
+def test_run_host_matches_device_path(lbm, kind):
+    """The host-buffer entry point (state in, n steps, moments out) gives the
+    bits of the same steps on device buffers."""
+    B, ny, nx = 2, 40, 200
     f = population_field(B, ny, nx, seed=51)
     th = torch.tensor(inputs.xavier_mlp(2, bias_scale=0.3, gain=2.0, out_scale=0.02), dtype=torch.float32, device=DEV)
     w = lbm.weights_struct(th)
-    lat = lbm.Lattice(nx, ny, B, device=DEV)
+    lat = lbm.Lattice(nx, ny, B, force_amp=1e-4, force_mode=1, device=DEV)
     lat.set_state(_dev(f))
-    lat.step(5, "mlp_f32", w)
+    lat.step(5, kind, w)
     r, vx, vy = (_np(t) for t in lat.moments())
     host = torch.tensor(f).pin_memory()
     outs = [torch.empty((B, ny, nx), dtype=torch.float32).pin_memory() for _ in range(3)]
-    lat2 = lbm.Lattice(nx, ny, B, device=DEV)
-    lat2.run_host(host, 5, "mlp_f32", w, *outs)
+    lat2 = lbm.Lattice(nx, ny, B, force_amp=1e-4, force_mode=1, device=DEV)
+    lat2.run_host(host, 5, kind, w, *outs)
     for a, b in zip((r, vx, vy), outs):
         assert np.array_equal(a, b.double().numpy())
 
