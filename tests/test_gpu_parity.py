@@ -172,15 +172,32 @@ def test_velocity_loss_parity(lbm):
     assert float(l2.item()) == float(loss.item())
 
 
-def test_unstable_state_sets_status(lbm):
-    n = 16
-    rho = np.ones((1, n, n))
-    ux = np.full((1, n, n), 0.5)  # |u| = 0.5 > 0.4
-    lat = lbm.Lattice(n, n, 1, device=DEV)
+@pytest.mark.parametrize("kind", ["bgk", "smag", "mlp_f32", "mlp_bf16"])
+@pytest.mark.parametrize("bad", ["fast", "nan"])
+def test_unstable_state_sets_status(lbm, kind, bad):
+    """Every step kernel flags a node whose velocity reaches 0.4 or is not
+    finite (one node of a 256 x 16 lattice, away from the tile edges), and the
+    flag stays until cleared."""
+    nx, ny = 256, 16
+    rho = np.ones((1, ny, nx))
+    ux = np.full((1, ny, nx), 0.01)
+    if bad == "fast":
+        ux[0, 7, 130] = 0.5  # |u| = 0.5 > 0.4
+    w = lbm.weights_struct(torch.tensor(inputs.xavier_mlp(2, out_scale=0.02),
+                                        dtype=torch.float32, device=DEV))
+    lat = lbm.Lattice(nx, ny, 1, smag_cs=0.1, device=DEV)
     lat.init_equilibrium(_dev(rho), _dev(ux), _dev(np.zeros_like(ux)))
-    lat.step(1, "bgk")
+    if bad == "nan":
+        f = lat.get_state()
+        f[0, 3, 7, 130] = float("nan")
+        lat.set_state(f.clone())
+    lat.step(1, kind, w)
     assert lat.status() == lbm.LBM_ERR_UNSTABLE
     lat.clear_status()
+    assert lat.status() == lbm.LBM_OK
+    # a stable lattice raises nothing
+    lat.init_equilibrium(_dev(rho), _dev(np.full_like(ux, 0.01)), _dev(np.zeros_like(ux)))
+    lat.step(2, kind, w)
     assert lat.status() == lbm.LBM_OK
 
 
